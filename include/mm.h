@@ -1,0 +1,198 @@
+/*
+ * mm.h -- C ABI of libmm, a GB300 (sm_103a) implementation of the RBF-FD
+ * stencil-weight pipeline of strong-form mesh-free methods (Slak & Kosec,
+ * "Medusa: a C++ library for solving PDEs using strong form mesh-free
+ * methods", arXiv 1912.13282):
+ *
+ *   nodes -> stencils (mm_knn_stencils, Section 2.1)
+ *         -> weights  (mm_rbffd_weights, Section 2.2.2, eq. rbf-system-aug)
+ *         -> operator (CSR, one value array per operator, Section 3.3)
+ *         -> application to fields (mm_apply_operator, mm_diffuse, Section 2.3.1)
+ *
+ * Conventions shared by every call:
+ *  - Device pointers are named d_*; everything else lives on the host.
+ *  - The caller allocates and owns every device buffer it passes.  The
+ *    library owns only the workspace inside an mm_ctx.
+ *  - Every call is enqueued on the context's CUDA stream and returns without
+ *    waiting for the GPU, except where a comment says it synchronises.
+ *    Argument checks that need only host data happen before anything is
+ *    enqueued.
+ *  - Return value: MM_OK (0) or a negative MM_E* code; mm_last_error() then
+ *    holds a message.  No C++ exception crosses this boundary.
+ *  - Per-node outcomes go to an optional int32 status array (MM_ST_*).
+ *  - Indices are 0-based; stencil row i lists node i first (the paper's
+ *    I(i)_1 = i becomes col[row_ptr[i]] == i).
+ *  - Points are float64, array-of-structures [N x dim], dim in {2, 3}.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define MM_OK 0
+#define MM_EBADARG -1     /* invalid argument (see mm_last_error)              */
+#define MM_ENOMEM -2      /* workspace allocation failed                       */
+#define MM_ECUDA -3       /* a CUDA runtime call failed                        */
+#define MM_EUNSUPPORTED -4 /* a size or option outside what this build handles */
+
+/* ------------------------------------------------------- per-node statuses */
+#define MM_ST_OK 0
+#define MM_ST_SINGULAR 1      /* pivot <= M*u*max|K|: weights set to 0         */
+#define MM_ST_NONCONVERGED 2  /* refinement did not converge (then fallback)   */
+#define MM_ST_FALLBACK 3      /* mixed/surrogate path: solved by the FP64 path */
+#define MM_ST_BADARG 4        /* bad stencil row (size, centre, index)         */
+#define MM_ST_DUPLICATE 5     /* kNN: another node coincides with this one     */
+#define MM_ST_ACCEPTED 6      /* surrogate: projected prediction accepted      */
+
+/* ------------------------------------------------------------ operator bits */
+#define MM_LAP 1u   /* Laplacian                                   */
+#define MM_DX 2u    /* d/dx                                        */
+#define MM_DY 4u    /* d/dy                                        */
+#define MM_DZ 8u    /* d/dz (dim 3)                                */
+#define MM_DN 16u   /* d/dn = sum_a n_a d/dx_a with the node normal */
+
+/* ------------------------------------------------------------ precisions */
+#define MM_FP64 0     /* plain FP64 solve                                      */
+#define MM_FP32_IR 1  /* FP32 LU + FP64-residual iterative refinement,
+                         condition-estimate / non-convergence fallback to FP64 */
+
+/* ------------------------------------------------------------ kNN methods */
+#define MM_KNN_AUTO 0
+#define MM_KNN_BRUTE 1  /* exhaustive scan of all nodes                     */
+#define MM_KNN_GRID 2   /* uniform-grid binning + ring search (exact)       */
+
+/* ------------------------------------------------------------ ctx options */
+#define MM_OPT_IR_TOL 1        /* IR stop: estimated rel. forward error (1e-9) */
+#define MM_OPT_IR_MAX_STEPS 2  /* IR residual evaluations at most (4)          */
+#define MM_OPT_KAPPA_MAX 3     /* fallback if kappa1_est * u32 exceeds (0.1)   */
+
+typedef struct mm_ctx mm_ctx;
+
+/*
+ * Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a
+ * cudaStream_t, NULL = legacy default stream).  *out receives the context.
+ * Errors: MM_EBADARG (out NULL), MM_ECUDA (device not usable).
+ */
+int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream);
+
+/* Free the context and its workspace (synchronises its stream).  NULL is a no-op. */
+void mm_ctx_destroy(mm_ctx *ctx);
+
+/* Switch the stream later calls enqueue on. */
+int mm_ctx_set_stream(mm_ctx *ctx, void *cuda_stream);
+
+/* Set a tuning option (MM_OPT_*).  Errors: MM_EBADARG for unknown keys or
+ * out-of-range values. */
+int mm_ctx_set_option(mm_ctx *ctx, int key, double value);
+
+/* Message of the last failed call on this context ("" if none).  The string
+ * is owned by the context and valid until its next call. */
+const char *mm_last_error(const mm_ctx *ctx);
+
+/* -------------------------------------------------------------- stencils */
+/*
+ * One block of query nodes for mm_knn_stencils: nodes q_begin..q_end-1 get
+ * stencils of n nodes, written row-major to d_idx[(q - q_begin) * n + j].
+ */
+typedef struct {
+    int64_t q_begin, q_end;
+    int32_t n;
+    int32_t *d_idx;
+} mm_knn_range;
+
+/*
+ * Stencils of the n closest nodes (Section 2.1, "some number of closest
+ * neighbours"; each node in its own stencil, first).  Candidates are all N
+ * nodes of d_pts [N x dim].  Row q lists q, then the n-1 other nodes in
+ * ascending (squared distance computed in FP64 as sum_a (x_a - c_a)^2 without
+ * fused multiply-add, node index).  This ranking is exact, so results are
+ * bit-identical to any other exact implementation of it.
+ *   method   MM_KNN_GRID (binned ring search), MM_KNN_BRUTE, or MM_KNN_AUTO.
+ *   d_status optional [N] int32: MM_ST_DUPLICATE where another node
+ *            coincides with the query, else MM_ST_OK (entries of nodes in
+ *            no range untouched).
+ * Requirements: 1 <= n <= 64, n <= N, N < 2^31, finite coordinates.
+ * Errors: MM_EBADARG, MM_EUNSUPPORTED (n > 64), MM_ENOMEM, MM_ECUDA.
+ */
+int mm_knn_stencils(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
+                    const mm_knn_range *ranges, int method, int32_t *d_status);
+
+/* ------------------------------------------------------------ CSR pattern */
+/* Device CSR stencil pattern: row i spans col[row_ptr[i] .. row_ptr[i+1]-1]. */
+typedef struct {
+    int64_t nrows;
+    int64_t nnz;
+    const int64_t *d_row_ptr;  /* [nrows + 1] */
+    const int32_t *d_col;      /* [nnz]       */
+} mm_csr_pattern;
+
+/* ---------------------------------------------------------------- weights */
+/*
+ * RBF-FD weights with polyharmonic splines phi(r) = r^k and monomials of
+ * total degree <= m (Section 2.2.2, eq. rbf-system-aug): for every row i in
+ * [row_begin, row_end) of the stencil pattern, with x_c the centre,
+ * s = max_j ||x_j - x_c|| and xi_j = (x_j - x_c)/s,
+ *     [A Q; Q^T 0] [w; lambda] = [l_phi; l_q],
+ *     A_ij = ||xi_i - xi_j||^k, Q_ib = q_b(xi_i),
+ * l_phi, l_q = the operator applied to each basis function at xi = 0; the
+ * stored weights are w / s^q (q = 2 for MM_LAP, 1 for first derivatives).
+ *
+ *   ops        bitmask of MM_LAP | MM_DX | MM_DY | MM_DZ | MM_DN.
+ *   k, m       odd k in {3, 5, 7}; 0 <= m <= 6; l = C(m + dim, dim).
+ *   d_pts      [N x dim] nodes; d_normals [N x dim] unit normals (needed
+ *              only with MM_DN; may be NULL otherwise).
+ *   stencils   rows are nodes; rows in range must have 1 <= n_i <= n_max,
+ *              col[row_ptr[i]] == i and indices in [0, N).
+ *   n_max      largest stencil size in the range; n_max + l <= 96.
+ *   precision  MM_FP64 or MM_FP32_IR.
+ *   d_vals     HOST array of device pointers, one per set bit of ops in bit
+ *              order; d_vals[r][row_ptr[i] + j] receives the weight of node j
+ *              of row i.  Several entries may alias the same array when
+ *              different row ranges write different operators into it.
+ *   d_status   optional [nrows] int32 (MM_ST_OK, MM_ST_SINGULAR, MM_ST_FALLBACK,
+ *              MM_ST_BADARG).  Singular or bad rows get zero weights.
+ * Errors: MM_EBADARG, MM_EUNSUPPORTED, MM_ENOMEM, MM_ECUDA.
+ */
+int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
+                     const double *d_pts, const double *d_normals,
+                     const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
+                     int n_max, int precision, double *const *d_vals, int32_t *d_status);
+
+/* ------------------------------------------------------ operator application */
+/*
+ * y = alpha * L u + beta * y with L the CSR operator (stencils, d_vals):
+ * (L u)_i = sum_j vals[row_ptr[i] + j] * u[col[row_ptr[i] + j]], the explicit
+ * evaluation w^T u_I(i) of Section 2.3.1.  d_u [ncols], d_y [nrows]; d_y must
+ * not alias d_u.  beta == 0 ignores the old contents of d_y.
+ * Errors: MM_EBADARG, MM_ECUDA.
+ */
+int mm_apply_operator(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+                      const double *d_u, double alpha, double beta, double *d_y);
+
+/*
+ * `steps` explicit Euler steps u <- u + dt * L u (eq. exp-start .. exp-end)
+ * on rows with d_fixed[i] == 0; rows with d_fixed[i] != 0 keep their value
+ * (Dirichlet nodes).  The operator must be square (nrows == length of d_u).
+ * d_work [nrows] float64 is caller-owned scratch.  The final field is in d_u.
+ * Errors: MM_EBADARG, MM_ECUDA.
+ */
+int mm_diffuse(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+               const uint8_t *d_fixed, double dt, int steps, double *d_u, double *d_work);
+
+/* ------------------------------------------------------------- measurement */
+/*
+ * Measured arithmetic peak of this GPU for the pipe `which` (0 = FP64 FMA,
+ * 1 = FP32 FMA), in FLOP/s (an FMA counts 2), from a dependent-chain-free
+ * FMA loop over every SM.  Synchronises.  Errors: MM_EBADARG, MM_ECUDA.
+ */
+int mm_measure_fma_peak(mm_ctx *ctx, int which, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libmm (include/mm.h).
+
+Only argument marshalling lives here: torch tensors are used for device
+memory and streams, every step of the pipeline runs in libmm's kernels.  If
+libmm.so has not been built (``paper_1912_13282_gb300._build.build()``) the
+first call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import _build
+
+MM_OK, MM_EBADARG, MM_ENOMEM, MM_ECUDA, MM_EUNSUPPORTED = 0, -1, -2, -3, -4
+ST_OK, ST_SINGULAR, ST_NONCONVERGED, ST_FALLBACK, ST_BADARG, ST_DUPLICATE, ST_ACCEPTED = range(7)
+LAP, DX, DY, DZ, DN = 1, 2, 4, 8, 16
+FP64, FP32_IR = 0, 1
+KNN_AUTO, KNN_BRUTE, KNN_GRID = 0, 1, 2
+OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX = 1, 2, 3
+
+EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
+           "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
+           "mm_diffuse", "mm_measure_fma_peak"]
+
+
+class KnnRange(C.Structure):
+    _fields_ = [("q_begin", C.c_int64), ("q_end", C.c_int64), ("n", C.c_int32),
+                ("d_idx", C.c_void_p)]
+
+
+class CsrPattern(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("nnz", C.c_int64), ("d_row_ptr", C.c_void_p),
+                ("d_col", C.c_void_p)]
+
+
+class MMError(RuntimeError):
+    pass
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmm.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise MMError(f"{_build.LIB} is missing: build it with "
+                          "paper_1912_13282_gb300._build.build() (needs nvcc)")
+        lib = C.CDLL(_build.LIB)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        lib.mm_ctx_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        lib.mm_ctx_destroy.argtypes = [vp]
+        lib.mm_ctx_destroy.restype = None
+        lib.mm_ctx_set_stream.argtypes = [vp, vp]
+        lib.mm_ctx_set_option.argtypes = [vp, C.c_int, dbl]
+        lib.mm_last_error.argtypes = [vp]
+        lib.mm_last_error.restype = C.c_char_p
+        lib.mm_knn_stencils.argtypes = [vp, C.c_int, i64, vp, C.c_int, C.POINTER(KnnRange),
+                                        C.c_int, vp]
+        lib.mm_rbffd_weights.argtypes = [vp, C.c_uint, C.c_int, C.c_int, C.c_int, i64, vp, vp,
+                                         C.POINTER(CsrPattern), i64, i64, C.c_int, C.c_int,
+                                         C.POINTER(vp), vp]
+        lib.mm_apply_operator.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, dbl, vp]
+        lib.mm_diffuse.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, C.c_int, vp, vp]
+        lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
+        for name in EXPORTS:
+            if name not in ("mm_ctx_destroy", "mm_last_error"):
+                getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, name, dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise MMError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise MMError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise MMError(f"{name} must be contiguous")
+    return t
+
+
+class Context:
+    """An mm_ctx bound to a device and a torch stream (default: current)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self._lib = load()
+        self.device = device
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        self.stream = s
+        h = C.c_void_p()
+        rc = self._lib.mm_ctx_create(C.byref(h), device, C.c_void_p(s.cuda_stream))
+        if rc != MM_OK:
+            raise MMError(f"mm_ctx_create failed ({rc})")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mm_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != MM_OK:
+            msg = self._lib.mm_last_error(self._h).decode(errors="replace")
+            raise MMError(f"libmm error {rc}: {msg}")
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self._lib.mm_ctx_set_stream(self._h, C.c_void_p(stream.cuda_stream)))
+
+    def set_option(self, key: int, value: float):
+        self._check(self._lib.mm_ctx_set_option(self._h, key, float(value)))
+
+    # ------------------------------------------------------------ stencils
+    def knn_stencils(self, pts: torch.Tensor, ranges, method: int = KNN_AUTO,
+                     status: torch.Tensor | None = None):
+        """ranges: list of (q_begin, q_end, n, out_idx int32 [(q_end-q_begin), n])."""
+        _dev(pts, "pts", torch.float64)
+        N, dim = pts.shape
+        arr = (KnnRange * max(1, len(ranges)))()
+        for i, (qb, qe, n, out) in enumerate(ranges):
+            _dev(out, "idx", torch.int32)
+            if out.numel() < (qe - qb) * n:
+                raise MMError("idx tensor too small")
+            arr[i] = KnnRange(qb, qe, n, out.data_ptr())
+        if status is not None:
+            _dev(status, "status", torch.int32)
+        self._check(self._lib.mm_knn_stencils(self._h, dim, N, _ptr(pts), len(ranges), arr,
+                                              method, _ptr(status)))
+
+    # ------------------------------------------------------------- weights
+    def rbffd_weights(self, ops: int, k: int, m: int, pts: torch.Tensor, row_ptr: torch.Tensor,
+                      col: torch.Tensor, vals, row_begin: int = 0, row_end: int | None = None,
+                      n_max: int | None = None, precision: int = FP64,
+                      normals: torch.Tensor | None = None, status: torch.Tensor | None = None):
+        """vals: list of float64 [nnz] tensors, one per set bit of ops (bit order)."""
+        _dev(pts, "pts", torch.float64)
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        N, dim = pts.shape
+        nrows = row_ptr.numel() - 1
+        if row_end is None:
+            row_end = nrows
+        if n_max is None:
+            raise MMError("n_max (largest stencil size in the row range) is required")
+        nbits = bin(ops).count("1")
+        if len(vals) != nbits:
+            raise MMError(f"{nbits} value arrays expected")
+        for v in vals:
+            _dev(v, "vals", torch.float64)
+        if normals is not None:
+            _dev(normals, "normals", torch.float64)
+        if status is not None:
+            _dev(status, "status", torch.int32)
+        pat = CsrPattern(nrows, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        vp = (C.c_void_p * max(1, nbits))(*[v.data_ptr() for v in vals])
+        self._check(self._lib.mm_rbffd_weights(self._h, ops, k, m, dim, N, _ptr(pts),
+                                               _ptr(normals), C.byref(pat), row_begin, row_end,
+                                               n_max, precision, vp, _ptr(status)))
+
+    # ------------------------------------------------- operator application
+    def apply_operator(self, row_ptr, col, vals, u, y, alpha=1.0, beta=0.0):
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        _dev(vals, "vals", torch.float64)
+        _dev(u, "u", torch.float64)
+        _dev(y, "y", torch.float64)
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        self._check(self._lib.mm_apply_operator(self._h, C.byref(pat), _ptr(vals), _ptr(u),
+                                                float(alpha), float(beta), _ptr(y)))
+
+    def diffuse(self, row_ptr, col, vals, fixed, dt, steps, u, work):
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        _dev(vals, "vals", torch.float64)
+        _dev(fixed, "fixed", torch.uint8)
+        _dev(u, "u", torch.float64)
+        _dev(work, "work", torch.float64)
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        self._check(self._lib.mm_diffuse(self._h, C.byref(pat), _ptr(vals), _ptr(fixed),
+                                         float(dt), int(steps), _ptr(u), _ptr(work)))
+
+    def measure_fma_peak(self, which: int) -> float:
+        out = C.c_double()
+        self._check(self._lib.mm_measure_fma_peak(self._h, which, C.byref(out)))
+        return out.value

@@ -1,0 +1,233 @@
+// The C ABI (mm.h): argument validation on the host, context and workspace
+// management, dispatch to the kernels.  No exception leaves this file.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <new>
+
+#include "mm_internal.cuh"
+
+int rbffd_init_device(mm_ctx *ctx);
+
+int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+char *mm_workspace(mm_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return ctx->ws;
+    size_t want = bytes + bytes / 4 + (1 << 20);
+    if (ctx->ws) {
+        cudaStreamSynchronize(ctx->stream);   // queued kernels may still use it
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return nullptr;
+    }
+    ctx->ws_bytes = want;
+    return ctx->ws;
+}
+
+namespace {
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(const mm_ctx *ctx) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (ctx && prev != ctx->device) cudaSetDevice(ctx->device);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool bad_dim(int dim) { return dim != 2 && dim != 3; }
+
+}  // namespace
+
+extern "C" {
+
+int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream) {
+    if (!out) return MM_EBADARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return MM_ECUDA;
+    }
+    mm_ctx *ctx = new (std::nothrow) mm_ctx();
+    if (!ctx) return MM_ENOMEM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(ctx);
+    int sms = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        delete ctx;
+        return MM_ECUDA;
+    }
+    ctx->num_sms = sms;
+    ctx->smem_optin = (size_t)optin;
+    if (rbffd_init_device(ctx) != MM_OK) {
+        delete ctx;
+        return MM_ECUDA;
+    }
+    *out = ctx;
+    return MM_OK;
+}
+
+void mm_ctx_destroy(mm_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    delete ctx;
+}
+
+int mm_ctx_set_stream(mm_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return MM_EBADARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return MM_OK;
+}
+
+int mm_ctx_set_option(mm_ctx *ctx, int key, double value) {
+    if (!ctx) return MM_EBADARG;
+    switch (key) {
+        case MM_OPT_IR_TOL:
+            if (!(value > 0 && value < 1)) return mm_fail(ctx, MM_EBADARG, "IR tolerance must be in (0,1)");
+            ctx->ir_tol = value;
+            return MM_OK;
+        case MM_OPT_IR_MAX_STEPS:
+            if (!(value >= 0 && value <= 32)) return mm_fail(ctx, MM_EBADARG, "IR steps must be in [0,32]");
+            ctx->ir_max_steps = (int)value;
+            return MM_OK;
+        case MM_OPT_KAPPA_MAX:
+            if (!(value > 0)) return mm_fail(ctx, MM_EBADARG, "kappa threshold must be > 0");
+            ctx->kappa_max = value;
+            return MM_OK;
+    }
+    return mm_fail(ctx, MM_EBADARG, "unknown option %d", key);
+}
+
+const char *mm_last_error(const mm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mm_knn_stencils(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
+                    const mm_knn_range *ranges, int method, int32_t *d_status) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (bad_dim(dim)) return mm_fail(ctx, MM_EBADARG, "dim must be 2 or 3");
+    if (N < 1 || N >= (int64_t(1) << 31)) return mm_fail(ctx, MM_EBADARG, "N out of range");
+    if (!d_pts) return mm_fail(ctx, MM_EBADARG, "d_pts is NULL");
+    if (nranges < 0 || (nranges > 0 && !ranges)) return mm_fail(ctx, MM_EBADARG, "bad ranges");
+    if (method < MM_KNN_AUTO || method > MM_KNN_GRID) return mm_fail(ctx, MM_EBADARG, "bad method");
+    for (int r = 0; r < nranges; ++r) {
+        const mm_knn_range &R = ranges[r];
+        if (R.q_begin < 0 || R.q_end < R.q_begin || R.q_end > N)
+            return mm_fail(ctx, MM_EBADARG, "range %d out of [0, N)", r);
+        if (R.n < 1) return mm_fail(ctx, MM_EBADARG, "range %d: n < 1", r);
+        if (R.n > 64) return mm_fail(ctx, MM_EUNSUPPORTED, "range %d: n = %d > 64", r, R.n);
+        if (R.n > N) return mm_fail(ctx, MM_EBADARG, "range %d: n > N", r);
+        if (R.q_end > R.q_begin && !R.d_idx) return mm_fail(ctx, MM_EBADARG, "range %d: d_idx NULL", r);
+    }
+    DeviceGuard g(ctx);
+    return knn_launch(ctx, dim, N, d_pts, nranges, ranges, method, d_status);
+}
+
+int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
+                     const double *d_pts, const double *d_normals, const mm_csr_pattern *stencils,
+                     int64_t row_begin, int64_t row_end, int n_max, int precision,
+                     double *const *d_vals, int32_t *d_status) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (bad_dim(dim)) return mm_fail(ctx, MM_EBADARG, "dim must be 2 or 3");
+    if (ops == 0 || ops >= 32u) return mm_fail(ctx, MM_EBADARG, "ops must be a nonzero MM_* bitmask");
+    if ((ops & MM_DZ) && dim != 3) return mm_fail(ctx, MM_EBADARG, "MM_DZ needs dim 3");
+    if ((ops & MM_DN) && !d_normals) return mm_fail(ctx, MM_EBADARG, "MM_DN needs d_normals");
+    if (k != 3 && k != 5 && k != 7) return mm_fail(ctx, MM_EBADARG, "k must be 3, 5 or 7");
+    if (m < 0 || m > 6) return mm_fail(ctx, MM_EBADARG, "m must be in [0, 6]");
+    if (N < 1 || N >= (int64_t(1) << 31) || !d_pts) return mm_fail(ctx, MM_EBADARG, "bad points");
+    if (!stencils || !stencils->d_row_ptr || !stencils->d_col)
+        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
+    if (row_begin < 0 || row_end < row_begin || row_end > stencils->nrows || stencils->nrows > N)
+        return mm_fail(ctx, MM_EBADARG, "row range out of [0, nrows]");
+    if (n_max < 1) return mm_fail(ctx, MM_EBADARG, "n_max < 1");
+    if (precision != MM_FP64 && precision != MM_FP32_IR)
+        return mm_fail(ctx, MM_EBADARG, "unknown precision %d", precision);
+    if (!d_vals) return mm_fail(ctx, MM_EBADARG, "d_vals is NULL");
+    WeightsJob job{};
+    job.ops = ops;
+    job.k = k;
+    job.m = m;
+    job.dim = dim;
+    job.N = N;
+    job.pts = d_pts;
+    job.normals = d_normals;
+    job.row_ptr = stencils->d_row_ptr;
+    job.col = stencils->d_col;
+    job.row_begin = row_begin;
+    job.row_end = row_end;
+    job.n_max = n_max;
+    job.status = d_status;
+    int r = 0;
+    for (int b = 0; b < 5; ++b) {
+        job.vals[b] = nullptr;
+        if (ops & (1u << b)) {
+            if (!d_vals[r]) return mm_fail(ctx, MM_EBADARG, "d_vals[%d] is NULL", r);
+            job.vals[b] = d_vals[r++];
+        }
+    }
+    if (n_max + mm_num_monomials(dim, m) > 96)
+        return mm_fail(ctx, MM_EUNSUPPORTED, "n_max + l = %d > 96", n_max + mm_num_monomials(dim, m));
+    DeviceGuard g(ctx);
+    return weights_launch(ctx, job, precision);
+}
+
+int mm_apply_operator(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+                      const double *d_u, double alpha, double beta, double *d_y) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (!stencils || !stencils->d_row_ptr || !stencils->d_col || stencils->nrows < 0)
+        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
+    if (stencils->nrows > 0 && (!d_vals || !d_u || !d_y))
+        return mm_fail(ctx, MM_EBADARG, "NULL vector or values");
+    if (d_u == d_y && stencils->nrows > 0) return mm_fail(ctx, MM_EBADARG, "d_y aliases d_u");
+    DeviceGuard g(ctx);
+    return spmv_launch(ctx, stencils, d_vals, d_u, alpha, beta, d_y);
+}
+
+int mm_diffuse(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+               const uint8_t *d_fixed, double dt, int steps, double *d_u, double *d_work) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (!stencils || !stencils->d_row_ptr || !stencils->d_col || stencils->nrows < 0)
+        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
+    if (steps < 0) return mm_fail(ctx, MM_EBADARG, "steps < 0");
+    if (stencils->nrows > 0 && (!d_vals || !d_fixed || !d_u || !d_work))
+        return mm_fail(ctx, MM_EBADARG, "NULL argument");
+    if (d_u == d_work && stencils->nrows > 0) return mm_fail(ctx, MM_EBADARG, "d_work aliases d_u");
+    DeviceGuard g(ctx);
+    return diffuse_launch(ctx, stencils, d_vals, d_fixed, dt, steps, d_u, d_work);
+}
+
+int mm_measure_fma_peak(mm_ctx *ctx, int which, double *flops_per_s) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if ((which != 0 && which != 1) || !flops_per_s) return mm_fail(ctx, MM_EBADARG, "bad arguments");
+    DeviceGuard g(ctx);
+    return peaks_measure(ctx, which, flops_per_s);
+}
+
+}  // extern "C"

@@ -1,0 +1,538 @@
+// Stencil selection: the n closest nodes of every query node (Section 2.1 of
+// the paper: stencils of closest neighbours, each node first in its own).
+//
+// Ranking: ascending (squared distance, node index).  The squared distance is
+// computed in FP64 exactly as sum_a (p_a - c_a)^2 in dimension order with
+// round-to-nearest and no fused multiply-add (__dsub_rn/__dmul_rn/__dadd_rn),
+// so any exact implementation of the same ranking gives bit-identical rows.
+//
+// Two search strategies, one warp per query, both exact:
+//  * grid: nodes are counting-sorted into a uniform grid (cell edge chosen
+//    from the mean density so a cell holds ~ppc nodes); the warp visits the
+//    query's cell and then Chebyshev rings of cells around it, skipping cells
+//    whose (slightly enlarged) box lies farther than the current n-th best,
+//    and stops once the ring boundary is farther than the n-th best.
+//  * brute: every node is a candidate (for small N).
+// The top n-1 list lives in registers across the warp (two slots per lane,
+// n <= 65) and is kept sorted by warp-wide insertion.
+#include <float.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "mm_internal.cuh"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct GridParams {
+    double lo[3];
+    double cell;
+    double inv_cell;
+    int dims[3];
+    int ncells;
+};
+
+// ------------------------------------------------------------------ binning
+template <int DIM>
+__global__ void k_bbox_partial(const double *__restrict__ pts, int64_t N, double *partial) {
+    double mn[DIM], mx[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { mn[a] = DBL_MAX; mx[a] = -DBL_MAX; }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            double v = pts[i * DIM + a];
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    }
+    __shared__ double smn[DIM][32], smx[DIM][32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        for (int o = 16; o; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(kFull, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+        }
+        if (lane == 0) { smn[a][w] = mn[a]; smx[a][w] = mx[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x >> 5;
+        for (int a = 0; a < DIM; ++a) {
+            double a0 = smn[a][0], a1 = smx[a][0];
+            for (int j = 1; j < nw; ++j) { a0 = fmin(a0, smn[a][j]); a1 = fmax(a1, smx[a][j]); }
+            partial[blockIdx.x * 2 * DIM + a] = a0;
+            partial[blockIdx.x * 2 * DIM + DIM + a] = a1;
+        }
+    }
+}
+
+// One thread: reduce the block partials, choose the cell edge so a cell holds
+// about `ppc` nodes on average, cap the cell count at `cap`.
+template <int DIM>
+__global__ void k_grid_params(const double *partial, int nparts, int64_t N, double ppc,
+                              int64_t cap, GridParams *gp) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo[DIM], hi[DIM], ext[DIM], emax = 0;
+    for (int a = 0; a < DIM; ++a) {
+        lo[a] = DBL_MAX; hi[a] = -DBL_MAX;
+        for (int j = 0; j < nparts; ++j) {
+            lo[a] = fmin(lo[a], partial[j * 2 * DIM + a]);
+            hi[a] = fmax(hi[a], partial[j * 2 * DIM + DIM + a]);
+        }
+        ext[a] = hi[a] - lo[a];
+        emax = fmax(emax, ext[a]);
+    }
+    if (!(emax > 0)) emax = 1.0;
+    double vol = 1.0;
+    for (int a = 0; a < DIM; ++a) {
+        ext[a] = fmax(ext[a], 1e-9 * emax);
+        vol *= ext[a];
+    }
+    double cells_target = fmax(1.0, (double)N / ppc);
+    double c = pow(vol / cells_target, 1.0 / DIM);
+    int dims[DIM];
+    for (int it = 0; it < 64; ++it) {
+        double prod = 1.0;
+        for (int a = 0; a < DIM; ++a) {
+            double d = ceil(ext[a] / c);
+            if (d < 1) d = 1;
+            if (d > 1 << 20) d = 1 << 20;
+            dims[a] = (int)d;
+            prod *= d;
+        }
+        if (prod <= (double)cap) break;
+        c *= pow(prod / (double)cap, 1.0 / DIM) * 1.01;
+    }
+    // Grid origin slightly below the box so no node sits on the low face.
+    for (int a = 0; a < 3; ++a) {
+        gp->lo[a] = a < DIM ? lo[a] - 1e-7 * c : 0.0;
+        gp->dims[a] = a < DIM ? dims[a] : 1;
+    }
+    gp->cell = c;
+    gp->inv_cell = 1.0 / c;
+    long long nc = 1;
+    for (int a = 0; a < DIM; ++a) nc *= dims[a];
+    gp->ncells = (int)nc;
+}
+
+template <int DIM>
+__device__ __forceinline__ int cell_coord(double x, int a, const GridParams &g) {
+    int i = (int)floor((x - g.lo[a]) * g.inv_cell);
+    return min(max(i, 0), g.dims[a] - 1);
+}
+
+template <int DIM>
+__global__ void k_cell_count(const double *__restrict__ pts, int64_t N, const GridParams *gp,
+                             int *cell_of, int *rank, int *count) {
+    GridParams g = *gp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int cid = 0;
+#pragma unroll
+        for (int a = DIM - 1; a >= 0; --a) cid = cid * g.dims[a] + cell_coord<DIM>(pts[i * DIM + a], a, g);
+        cell_of[i] = cid;
+        rank[i] = atomicAdd(&count[cid], 1);
+    }
+}
+
+// Exclusive scan of count[0..n) into start[0..n] in three passes.
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ int block_exclusive_scan(int v, int *sh, int *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < (blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    int base = w > 0 ? sh[w - 1] : 0;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void k_scan_tiles(const int *count, const GridParams *gp, int *start, int *tile_sum) {
+    __shared__ int sh[32];
+    int n = gp->ncells;
+    int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems], s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = base + j < n ? count[base + j] : 0;
+        s += v[j];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, sh, &total);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) start[base + j] = ex;
+        ex += v[j];
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int *tile_sum, int ntiles, const GridParams *gp, int *start) {
+    __shared__ int sh[32];
+    int carry = 0;
+    for (int b = 0; b < ntiles; b += blockDim.x) {
+        int v = b + threadIdx.x < ntiles ? tile_sum[b + threadIdx.x] : 0;
+        int total;
+        int ex = block_exclusive_scan(v, sh, &total);
+        if (b + threadIdx.x < ntiles) tile_sum[b + threadIdx.x] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) start[gp->ncells] = carry;
+}
+
+__global__ void k_scan_add(const int *tile_sum, const GridParams *gp, int *start) {
+    int n = gp->ncells;
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int add = tile_sum[blockIdx.x];
+    for (int j = threadIdx.x; j < kScanTile; j += blockDim.x)
+        if (base + j < n) start[base + j] += add;
+}
+
+template <int DIM>
+__global__ void k_scatter(const double *__restrict__ pts, int64_t N, const int *cell_of,
+                          const int *rank, const int *start, double *spts, int *sidx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int d = start[cell_of[i]] + rank[i];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) spts[(int64_t)d * DIM + a] = pts[i * DIM + a];
+        sidx[d] = (int)i;
+    }
+}
+
+// ------------------------------------------------------------- the top list
+__device__ __forceinline__ bool key_lt(double da, int ia, double db, int ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+// Sorted list of the K best (d2, index) keys; slot s on lane s (lo) and on
+// lane s-32 (hi).  Empty slots hold (+inf, INT_MAX).
+struct TopList {
+    double dlo, dhi;
+    int ilo, ihi;
+    int K;
+
+    __device__ void init(int k) {
+        K = k;
+        dlo = dhi = __longlong_as_double(0x7ff0000000000000LL);
+        ilo = ihi = 0x7fffffff;
+    }
+    // Key of slot K-1 (the worst kept), broadcast to all lanes.
+    __device__ void worst(double &d, int &i) const {
+        if (K == 0) { d = -1.0; i = -1; return; }
+        int s = K - 1;
+        int src = s & 31;
+        double dv = s < 32 ? dlo : dhi;
+        int iv = s < 32 ? ilo : ihi;
+        d = __shfl_sync(kFull, dv, src);
+        i = __shfl_sync(kFull, iv, src);
+    }
+    // Insert a warp-uniform key known to be better than the worst.
+    __device__ void insert(double d, int idx) {
+        int lane = threadIdx.x & 31;
+        unsigned blo = __ballot_sync(kFull, key_lt(dlo, ilo, d, idx));
+        unsigned bhi = __ballot_sync(kFull, key_lt(dhi, ihi, d, idx));
+        int pos = __popc(blo) + __popc(bhi);
+        double pdlo = __shfl_up_sync(kFull, dlo, 1);
+        int pilo = __shfl_up_sync(kFull, ilo, 1);
+        double pdhi = __shfl_up_sync(kFull, dhi, 1);
+        int pihi = __shfl_up_sync(kFull, ihi, 1);
+        double d31 = __shfl_sync(kFull, dlo, 31);
+        int i31 = __shfl_sync(kFull, ilo, 31);
+        if (lane == 0) { pdhi = d31; pihi = i31; }
+        int slo = lane, shi = lane + 32;
+        if (shi > pos) { dhi = pdhi; ihi = pihi; }
+        if (shi == pos) { dhi = d; ihi = idx; }
+        if (slo > pos) { dlo = pdlo; ilo = pilo; }
+        if (slo == pos) { dlo = d; ilo = idx; }
+    }
+};
+
+template <int DIM>
+__device__ __forceinline__ double dist2_rn(const double *p, const double *c) {
+    double t = __dsub_rn(p[0], c[0]);
+    double s = __dmul_rn(t, t);
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+        double u = __dsub_rn(p[a], c[a]);
+        s = __dadd_rn(s, __dmul_rn(u, u));
+    }
+    return s;
+}
+
+// Offer one candidate per lane (valid lanes only); inserts those that beat the
+// current worst, best-first order not required.
+__device__ __forceinline__ void offer(TopList &tl, bool valid, double d, int idx, double &wd,
+                                      int &wi) {
+    unsigned m = __ballot_sync(kFull, valid && key_lt(d, idx, wd, wi));
+    while (m) {
+        int src = __ffs(m) - 1;
+        m &= m - 1;
+        double cd = __shfl_sync(kFull, d, src);
+        int ci = __shfl_sync(kFull, idx, src);
+        if (key_lt(cd, ci, wd, wi)) {
+            tl.insert(cd, ci);
+            tl.worst(wd, wi);
+        }
+    }
+}
+
+__device__ __forceinline__ void write_row(const TopList &tl, int64_t q, int n, int32_t *out_row,
+                                          int32_t *status, bool dup) {
+    int lane = threadIdx.x & 31;
+    if (lane == 0) out_row[0] = (int32_t)q;
+    int K = n - 1;
+    bool full = true;
+    if (lane < K) {
+        out_row[1 + lane] = tl.ilo == 0x7fffffff ? -1 : tl.ilo;
+        full &= tl.ilo != 0x7fffffff;
+    }
+    if (lane + 32 < K) {
+        out_row[33 + lane] = tl.ihi == 0x7fffffff ? -1 : tl.ihi;
+        full &= tl.ihi != 0x7fffffff;
+    }
+    full = __all_sync(kFull, full);
+    if (status && lane == 0) status[q] = dup ? MM_ST_DUPLICATE : (full ? MM_ST_OK : MM_ST_BADARG);
+}
+
+// ---------------------------------------------------------- grid ring search
+template <int DIM>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__restrict__ start,
+           const double *__restrict__ spts, const int *__restrict__ sidx, int64_t q_begin,
+           int64_t q_end, int n, int32_t *__restrict__ out, int32_t *status) {
+    const GridParams g = *gp;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double slack = 1e-9 * g.cell;
+    for (int64_t q = q_begin + warp0; q < q_end; q += nwarps) {
+        double c[DIM];
+        int cq[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = pts[q * DIM + a];
+            cq[a] = cell_coord<DIM>(c[a], a, g);
+        }
+        TopList tl;
+        tl.init(n - 1);
+        double wd;
+        int wi;
+        tl.worst(wd, wi);
+        bool dup = false;
+        int maxdim = 0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) maxdim = max(maxdim, g.dims[a]);
+        for (int t = 0; t <= maxdim; ++t) {
+            const int side = 2 * t + 1;
+            int ncube = side;
+#pragma unroll
+            for (int a = 1; a < DIM; ++a) ncube *= side;
+            for (int u0 = 0; u0 < ncube; u0 += 32) {
+                int u = u0 + lane;
+                int cstart = 0, ccount = 0;
+                if (u < ncube) {
+                    int off[DIM], rem = u, cheb = 0;
+                    bool inside = true;
+                    int cid = 0;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        off[a] = rem % side - t;
+                        rem /= side;
+                        cheb = max(cheb, abs(off[a]));
+                    }
+                    double md2 = 0.0;
+#pragma unroll
+                    for (int a = DIM - 1; a >= 0; --a) {
+                        int ca = cq[a] + off[a];
+                        inside &= (ca >= 0 && ca < g.dims[a]);
+                        cid = cid * g.dims[a] + ca;
+                        double blo = g.lo[a] + ca * g.cell - slack;
+                        double bhi = g.lo[a] + (ca + 1) * g.cell + slack;
+                        double gap = fmax(0.0, fmax(blo - c[a], c[a] - bhi));
+                        md2 += gap * gap;
+                    }
+                    if (inside && cheb == t && !(md2 * (1.0 - 1e-12) > wd)) {
+                        cstart = start[cid];
+                        ccount = start[cid + 1] - cstart;
+                    }
+                }
+                // inclusive scan of counts over the warp
+                int incl = ccount;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int total = __shfl_sync(kFull, incl, 31);
+                for (int p0 = 0; p0 < total; p0 += 32) {
+                    int p = p0 + lane;
+                    int owner = 0;
+#pragma unroll
+                    for (int step = 16; step; step >>= 1) {
+                        int probe = __shfl_sync(kFull, incl, owner + step - 1);
+                        if (probe <= p) owner += step;
+                    }
+                    int os = __shfl_sync(kFull, cstart, owner);
+                    int oi = __shfl_sync(kFull, incl, owner);
+                    int oc = __shfl_sync(kFull, ccount, owner);
+                    bool valid = p < total;
+                    double d2 = 0.0;
+                    int idx = -1;
+                    if (valid) {
+                        int sp = os + (p - (oi - oc));
+                        idx = sidx[sp];
+                        d2 = dist2_rn<DIM>(spts + (int64_t)sp * DIM, c);
+                        if (idx == (int)q) valid = false;
+                        else if (d2 == 0.0) dup = true;
+                    }
+                    offer(tl, valid, d2, idx, wd, wi);
+                }
+            }
+            // stop once every unvisited cell is provably farther than the worst kept
+            bool covers = true;
+            double bd = DBL_MAX;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                bool lo_edge = cq[a] - t <= 0, hi_edge = cq[a] + t >= g.dims[a] - 1;
+                covers &= lo_edge && hi_edge;
+                if (!lo_edge) bd = fmin(bd, c[a] - (g.lo[a] + (cq[a] - t) * g.cell) - slack);
+                if (!hi_edge) bd = fmin(bd, g.lo[a] + (cq[a] + t + 1) * g.cell + slack - c[a]);
+            }
+            if (covers) break;
+            bd = fmax(bd, 0.0);
+            if (bd * bd * (1.0 - 1e-12) > wd) break;
+        }
+        dup = __any_sync(kFull, dup);
+        write_row(tl, q, n, out + (q - q_begin) * n, status, dup);
+    }
+}
+
+// ----------------------------------------------------------------- brute force
+template <int DIM>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_knn_brute(const double *__restrict__ pts, int64_t N, int64_t q_begin, int64_t q_end, int n,
+            int32_t *__restrict__ out, int32_t *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = q_begin + warp0; q < q_end; q += nwarps) {
+        double c[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) c[a] = pts[q * DIM + a];
+        TopList tl;
+        tl.init(n - 1);
+        double wd;
+        int wi;
+        tl.worst(wd, wi);
+        bool dup = false;
+        for (int64_t j0 = 0; j0 < N; j0 += 32) {
+            int64_t j = j0 + lane;
+            bool valid = j < N && j != q;
+            double d2 = 0.0;
+            if (valid) {
+                d2 = dist2_rn<DIM>(pts + j * DIM, c);
+                if (d2 == 0.0) dup = true;
+            }
+            offer(tl, valid, d2, (int)j, wd, wi);
+        }
+        dup = __any_sync(kFull, dup);
+        write_row(tl, q, n, out + (q - q_begin) * n, status, dup);
+    }
+}
+
+template <int DIM>
+int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_knn_range *ranges,
+             int method, int32_t *d_status) {
+    int nmax = 0;
+    for (int r = 0; r < nranges; ++r) nmax = max(nmax, (int)ranges[r].n);
+    cudaStream_t st = ctx->stream;
+    const int qblocks = ctx->num_sms * 16;
+    if (method == MM_KNN_AUTO) method = N <= 4096 ? MM_KNN_BRUTE : MM_KNN_GRID;
+    if (method == MM_KNN_BRUTE) {
+        for (int r = 0; r < nranges; ++r) {
+            const mm_knn_range &R = ranges[r];
+            if (R.q_end <= R.q_begin) continue;
+            int64_t warps = R.q_end - R.q_begin;
+            int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
+            k_knn_brute<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, N, R.q_begin, R.q_end,
+                                                                     R.n, R.d_idx, d_status);
+            MM_LAUNCH_CHECK(ctx);
+        }
+        return MM_OK;
+    }
+    // ---- grid build
+    double ppc = fmax(2.0, nmax / double(1 << DIM));
+    int64_t cap = (int64_t)(4.0 * N / ppc) + 64;
+    const int bb_blocks = min(ctx->num_sms * 2, (int)((N + 255) / 256) + 1);
+    int ntiles = (int)((cap + kScanTile - 1) / kScanTile);
+    WsCarve wc;
+    size_t o_part = wc.take<double>((size_t)bb_blocks * 2 * DIM);
+    size_t o_gp = wc.take<GridParams>(1);
+    size_t o_count = wc.take<int>((size_t)cap + 1);
+    size_t o_start = wc.take<int>((size_t)cap + 1);
+    size_t o_cellof = wc.take<int>((size_t)N);
+    size_t o_rank = wc.take<int>((size_t)N);
+    size_t o_spts = wc.take<double>((size_t)N * DIM);
+    size_t o_sidx = wc.take<int>((size_t)N);
+    size_t o_tiles = wc.take<int>((size_t)ntiles + 1);
+    char *ws = mm_workspace(ctx, wc.off);
+    if (!ws) return mm_fail(ctx, MM_ENOMEM, "knn workspace of %zu bytes", wc.off);
+    double *part = (double *)(ws + o_part);
+    GridParams *gp = (GridParams *)(ws + o_gp);
+    int *count = (int *)(ws + o_count), *start = (int *)(ws + o_start);
+    int *cellof = (int *)(ws + o_cellof), *rank = (int *)(ws + o_rank);
+    double *spts = (double *)(ws + o_spts);
+    int *sidx = (int *)(ws + o_sidx), *tiles = (int *)(ws + o_tiles);
+    const int eb = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 8);
+    k_bbox_partial<DIM><<<bb_blocks, 256, 0, st>>>(d_pts, N, part);
+    k_grid_params<DIM><<<1, 32, 0, st>>>(part, bb_blocks, N, ppc, cap, gp);
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(cap + 1), st));
+    k_cell_count<DIM><<<eb, 256, 0, st>>>(d_pts, N, gp, cellof, rank, count);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count, gp, start, tiles);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(tiles, ntiles, gp, start);
+    k_scan_add<<<ntiles, kScanThreads, 0, st>>>(tiles, gp, start);
+    k_scatter<DIM><<<eb, 256, 0, st>>>(d_pts, N, cellof, rank, start, spts, sidx);
+    MM_LAUNCH_CHECK(ctx);
+    for (int r = 0; r < nranges; ++r) {
+        const mm_knn_range &R = ranges[r];
+        if (R.q_end <= R.q_begin) continue;
+        int64_t warps = R.q_end - R.q_begin;
+        int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
+        k_knn_grid<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, gp, start, spts, sidx,
+                                                                R.q_begin, R.q_end, R.n, R.d_idx,
+                                                                d_status);
+        MM_LAUNCH_CHECK(ctx);
+    }
+    return MM_OK;
+}
+
+}  // namespace
+
+int knn_launch(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
+               const mm_knn_range *ranges, int method, int32_t *d_status) {
+    if (dim == 2) return knn_impl<2>(ctx, N, d_pts, nranges, ranges, method, d_status);
+    return knn_impl<3>(ctx, N, d_pts, nranges, ranges, method, d_status);
+}

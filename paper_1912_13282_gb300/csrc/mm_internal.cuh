@@ -1,0 +1,86 @@
+// Internal declarations shared by the libmm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mm.h"
+
+struct mm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    // growable device workspace (bump-allocated per call)
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    // options
+    double ir_tol = 1e-9;
+    int ir_max_steps = 4;
+    double kappa_max = 0.1;
+};
+
+// Records a message and returns `code`.
+int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...);
+
+// Ensures the workspace holds at least `bytes`; returns its base or nullptr.
+char *mm_workspace(mm_ctx *ctx, size_t bytes);
+
+// Bump allocator over the workspace, 256-byte aligned slices.
+struct WsCarve {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        size_t o = off;
+        off += (count * sizeof(T) + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+#define MM_CUDA_CHECK(ctx, expr)                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return mm_fail((ctx), MM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));   \
+    } while (0)
+
+#define MM_LAUNCH_CHECK(ctx)                                                            \
+    do {                                                                                \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess)                                                          \
+            return mm_fail((ctx), MM_ECUDA, "kernel launch: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---------------------------------------------------------------- launchers
+int knn_launch(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
+               const mm_knn_range *ranges, int method, int32_t *d_status);
+
+struct WeightsJob {
+    unsigned ops;
+    int k, m, dim;
+    int64_t N;
+    const double *pts, *normals;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    int64_t row_begin, row_end;
+    int n_max;
+    double *vals[5];  // per operator bit (nullptr if not requested)
+    int32_t *status;
+};
+
+int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision);
+int spmv_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const double *u,
+                double alpha, double beta, double *y);
+int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals,
+                   const uint8_t *fixed, double dt, int steps, double *u, double *work);
+int peaks_measure(mm_ctx *ctx, int which, double *flops_per_s);
+
+// Number of monomials of total degree <= m in dim variables: C(m+dim, dim).
+inline int mm_num_monomials(int dim, int m) {
+    long long c = 1;
+    for (int i = 1; i <= dim; ++i) c = c * (m + i) / i;
+    return (int)c;
+}
