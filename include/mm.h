@@ -163,6 +163,34 @@ int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N
                      const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
                      int n_max, int precision, double *const *d_vals, int32_t *d_status);
 
+/*
+ * Allocation-free variant of mm_rbffd_weights with precision MM_FP32_IR.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory when they call in -- e.g. a process whose memory pool has
+ * already reserved the GPU's memory (a cudaMalloc there fails or fragments
+ * it), or a latency-critical loop where a cudaFree would synchronise the
+ * whole device.  The regular call may grow the context workspace to hold the
+ * queue of stencils handed from the FP32 solve to the FP64 solve; this one
+ * keeps that queue in a fixed array of 1 + 2^20 int32 (4 MiB) inside the
+ * library image, present on every GPU that loads the library until exit.
+ *   Same arguments and results as mm_rbffd_weights(..., MM_FP32_IR, ...).
+ *   At most 2^20 rows per call (row_end - row_begin); larger ranges fail
+ *   with MM_EUNSUPPORTED before anything is enqueued.
+ *   Calls no cudaMalloc, cudaFree or allocating library routine.  The first
+ *   call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   and caches it; make that first call before any stream capture.
+ *   Every call shares the array, which keeps the last call's contents; the
+ *   call clears the queue length on its stream first.  Calls whose GPU work
+ *   overlaps (different streams, or different contexts on one device) race on
+ *   the queue: serialise them.
+ * Errors: as mm_rbffd_weights; MM_ECUDA if the address lookup fails.
+ */
+int mm_rbffd_weights_ir_noalloc(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
+                                const double *d_pts, const double *d_normals,
+                                const mm_csr_pattern *stencils, int64_t row_begin,
+                                int64_t row_end, int n_max, double *const *d_vals,
+                                int32_t *d_status);
+
 /* ------------------------------------------------------ operator application */
 /*
  * y = alpha * L u + beta * y with L the CSR operator (stencils, d_vals):

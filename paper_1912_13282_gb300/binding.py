@@ -24,7 +24,7 @@ OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX = 1, 2, 3
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
-           "mm_diffuse", "mm_measure_fma_peak"]
+           "mm_diffuse", "mm_measure_fma_peak", "mm_rbffd_weights_ir_noalloc"]
 
 
 class KnnRange(C.Structure):
@@ -72,6 +72,9 @@ def load():
         lib.mm_rbffd_weights.argtypes = [vp, C.c_uint, C.c_int, C.c_int, C.c_int, i64, vp, vp,
                                          C.POINTER(CsrPattern), i64, i64, C.c_int, C.c_int,
                                          C.POINTER(vp), vp]
+        lib.mm_rbffd_weights_ir_noalloc.argtypes = [vp, C.c_uint, C.c_int, C.c_int, C.c_int, i64,
+                                                    vp, vp, C.POINTER(CsrPattern), i64, i64,
+                                                    C.c_int, C.POINTER(vp), vp]
         lib.mm_apply_operator.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, dbl, vp]
         lib.mm_diffuse.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, C.c_int, vp, vp]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
@@ -181,6 +184,27 @@ class Context:
         self._check(self._lib.mm_rbffd_weights(self._h, ops, k, m, dim, N, _ptr(pts),
                                                _ptr(normals), C.byref(pat), row_begin, row_end,
                                                n_max, precision, vp, _ptr(status)))
+
+    def rbffd_weights_ir_noalloc(self, ops: int, k: int, m: int, pts, row_ptr, col, vals,
+                                 row_begin: int = 0, row_end: int | None = None,
+                                 n_max: int | None = None, normals=None, status=None):
+        """mm_rbffd_weights_ir_noalloc: FP32 + FP64 refinement without any
+        device allocation (at most 2^20 rows per call; see include/mm.h)."""
+        _dev(pts, "pts", torch.float64)
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        N, dim = pts.shape
+        nrows = row_ptr.numel() - 1
+        row_end = nrows if row_end is None else row_end
+        if n_max is None:
+            raise MMError("n_max is required")
+        for v in vals:
+            _dev(v, "vals", torch.float64)
+        pat = CsrPattern(nrows, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        vp = (C.c_void_p * max(1, len(vals)))(*[v.data_ptr() for v in vals])
+        self._check(self._lib.mm_rbffd_weights_ir_noalloc(
+            self._h, ops, k, m, dim, N, _ptr(pts), _ptr(normals), C.byref(pat), row_begin,
+            row_end, n_max, vp, _ptr(status)))
 
     # ------------------------------------------------- operator application
     def apply_operator(self, row_ptr, col, vals, u, y, alpha=1.0, beta=0.0):

@@ -41,22 +41,54 @@ char *mm_workspace(mm_ctx *ctx, size_t bytes) {
 
 namespace {
 
-// Makes the context's device current for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(const mm_ctx *ctx) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (ctx && prev != ctx->device) cudaSetDevice(ctx->device);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 bool bad_dim(int dim) { return dim != 2 && dim != 3; }
 
 }  // namespace
+
+int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
+                          const double *d_pts, const double *d_normals,
+                          const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
+                          int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job) {
+    if (bad_dim(dim)) return mm_fail(ctx, MM_EBADARG, "dim must be 2 or 3");
+    if (ops == 0 || ops >= 32u) return mm_fail(ctx, MM_EBADARG, "ops must be a nonzero MM_* bitmask");
+    if ((ops & MM_DZ) && dim != 3) return mm_fail(ctx, MM_EBADARG, "MM_DZ needs dim 3");
+    if ((ops & MM_DN) && !d_normals) return mm_fail(ctx, MM_EBADARG, "MM_DN needs d_normals");
+    if (k != 3 && k != 5 && k != 7) return mm_fail(ctx, MM_EBADARG, "k must be 3, 5 or 7");
+    if (m < 0 || m > 6) return mm_fail(ctx, MM_EBADARG, "m must be in [0, 6]");
+    if (N < 1 || N >= (int64_t(1) << 31) || !d_pts) return mm_fail(ctx, MM_EBADARG, "bad points");
+    if (!stencils || !stencils->d_row_ptr || !stencils->d_col)
+        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
+    if (row_begin < 0 || row_end < row_begin || row_end > stencils->nrows || stencils->nrows > N)
+        return mm_fail(ctx, MM_EBADARG, "row range out of [0, nrows]");
+    if (n_max < 1) return mm_fail(ctx, MM_EBADARG, "n_max < 1");
+    if (!d_vals) return mm_fail(ctx, MM_EBADARG, "d_vals is NULL");
+    WeightsJob &J = *job;
+    J = WeightsJob{};
+    J.ops = ops;
+    J.k = k;
+    J.m = m;
+    J.dim = dim;
+    J.N = N;
+    J.pts = d_pts;
+    J.normals = d_normals;
+    J.row_ptr = stencils->d_row_ptr;
+    J.col = stencils->d_col;
+    J.row_begin = row_begin;
+    J.row_end = row_end;
+    J.n_max = n_max;
+    J.status = d_status;
+    int r = 0;
+    for (int b = 0; b < 5; ++b) {
+        J.vals[b] = nullptr;
+        if (ops & (1u << b)) {
+            if (!d_vals[r]) return mm_fail(ctx, MM_EBADARG, "d_vals[%d] is NULL", r);
+            J.vals[b] = d_vals[r++];
+        }
+    }
+    if (n_max + mm_num_monomials(dim, m) > 96)
+        return mm_fail(ctx, MM_EUNSUPPORTED, "n_max + l = %d > 96", n_max + mm_num_monomials(dim, m));
+    return MM_OK;
+}
 
 extern "C" {
 
@@ -152,45 +184,12 @@ int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N
                      double *const *d_vals, int32_t *d_status) {
     if (!ctx) return MM_EBADARG;
     ctx->err.clear();
-    if (bad_dim(dim)) return mm_fail(ctx, MM_EBADARG, "dim must be 2 or 3");
-    if (ops == 0 || ops >= 32u) return mm_fail(ctx, MM_EBADARG, "ops must be a nonzero MM_* bitmask");
-    if ((ops & MM_DZ) && dim != 3) return mm_fail(ctx, MM_EBADARG, "MM_DZ needs dim 3");
-    if ((ops & MM_DN) && !d_normals) return mm_fail(ctx, MM_EBADARG, "MM_DN needs d_normals");
-    if (k != 3 && k != 5 && k != 7) return mm_fail(ctx, MM_EBADARG, "k must be 3, 5 or 7");
-    if (m < 0 || m > 6) return mm_fail(ctx, MM_EBADARG, "m must be in [0, 6]");
-    if (N < 1 || N >= (int64_t(1) << 31) || !d_pts) return mm_fail(ctx, MM_EBADARG, "bad points");
-    if (!stencils || !stencils->d_row_ptr || !stencils->d_col)
-        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
-    if (row_begin < 0 || row_end < row_begin || row_end > stencils->nrows || stencils->nrows > N)
-        return mm_fail(ctx, MM_EBADARG, "row range out of [0, nrows]");
-    if (n_max < 1) return mm_fail(ctx, MM_EBADARG, "n_max < 1");
     if (precision != MM_FP64 && precision != MM_FP32_IR)
         return mm_fail(ctx, MM_EBADARG, "unknown precision %d", precision);
-    if (!d_vals) return mm_fail(ctx, MM_EBADARG, "d_vals is NULL");
     WeightsJob job{};
-    job.ops = ops;
-    job.k = k;
-    job.m = m;
-    job.dim = dim;
-    job.N = N;
-    job.pts = d_pts;
-    job.normals = d_normals;
-    job.row_ptr = stencils->d_row_ptr;
-    job.col = stencils->d_col;
-    job.row_begin = row_begin;
-    job.row_end = row_end;
-    job.n_max = n_max;
-    job.status = d_status;
-    int r = 0;
-    for (int b = 0; b < 5; ++b) {
-        job.vals[b] = nullptr;
-        if (ops & (1u << b)) {
-            if (!d_vals[r]) return mm_fail(ctx, MM_EBADARG, "d_vals[%d] is NULL", r);
-            job.vals[b] = d_vals[r++];
-        }
-    }
-    if (n_max + mm_num_monomials(dim, m) > 96)
-        return mm_fail(ctx, MM_EUNSUPPORTED, "n_max + l = %d > 96", n_max + mm_num_monomials(dim, m));
+    int rc = weights_job_from_args(ctx, ops, k, m, dim, N, d_pts, d_normals, stencils, row_begin,
+                                   row_end, n_max, d_vals, d_status, &job);
+    if (rc != MM_OK) return rc;
     DeviceGuard g(ctx);
     return weights_launch(ctx, job, precision);
 }

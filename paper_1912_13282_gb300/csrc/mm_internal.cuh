@@ -72,11 +72,31 @@ struct WeightsJob {
 };
 
 int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision);
+int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, int *fb_count,
+                           int *fb_list);
 int spmv_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const double *u,
                 double alpha, double beta, double *y);
 int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals,
                    const uint8_t *fixed, double dt, int steps, double *u, double *work);
 int peaks_measure(mm_ctx *ctx, int which, double *flops_per_s);
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(const mm_ctx *ctx) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (ctx && prev != ctx->device) cudaSetDevice(ctx->device);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
+                          const double *d_pts, const double *d_normals,
+                          const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
+                          int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job);
 
 // Number of monomials of total degree <= m in dim variables: C(m+dim, dim).
 inline int mm_num_monomials(int dim, int m) {

@@ -696,7 +696,11 @@ int rbffd_init_device(mm_ctx *ctx) {
     return MM_OK;
 }
 
-int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision) {
+// fb_count/fb_list: caller-provided queue for rows the FP32 path hands to the
+// FP64 solve ([1] and [rows] ints); nullptr takes them from the context
+// workspace.
+int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, int *fb_count,
+                           int *fb_list) {
     const int dim = job.dim;
     const int l = mm_num_monomials(dim, job.m);
     WParams P{};
@@ -758,13 +762,18 @@ int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision) {
     if (precision == MM_FP64) return launch_fp64(nullptr, nullptr, rows);
 
     // mixed: FP32 LU + FP64-residual refinement, queue stragglers for FP64
-    WsCarve wc;
-    size_t o_cnt = wc.take<int>(1);
-    size_t o_list = wc.take<int>((size_t)rows);
-    char *ws = mm_workspace(ctx, wc.off);
-    if (!ws) return mm_fail(ctx, MM_ENOMEM, "weights workspace of %zu bytes", wc.off);
-    P.fb_count = (int *)(ws + o_cnt);
-    P.fb_list = (int *)(ws + o_list);
+    if (fb_count && fb_list) {
+        P.fb_count = fb_count;
+        P.fb_list = fb_list;
+    } else {
+        WsCarve wc;
+        size_t o_cnt = wc.take<int>(1);
+        size_t o_list = wc.take<int>((size_t)rows);
+        char *ws = mm_workspace(ctx, wc.off);
+        if (!ws) return mm_fail(ctx, MM_ENOMEM, "weights workspace of %zu bytes", wc.off);
+        P.fb_count = (int *)(ws + o_cnt);
+        P.fb_list = (int *)(ws + o_list);
+    }
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(P.fb_count, 0, sizeof(int), st));
     const size_t wm = mixed_warp_bytes(P.M_max, P.pitch64, P.pitch32, P.n_max, dim, R);
     int wpb = warps_for(wm);
@@ -780,4 +789,8 @@ int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision) {
     }
     MM_LAUNCH_CHECK(ctx);
     return launch_fp64(P.fb_list, P.fb_count, rows);
+}
+
+int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision) {
+    return weights_launch_scratch(ctx, job, precision, nullptr, nullptr);
 }
