@@ -45,7 +45,7 @@ __constant__ MonoTable c_mono;
 struct WParams {
     int dim, k, m, l, R;
     int n_max, M_max;
-    int pitch64, pitch32;      // shared-memory row pitches (elements)
+    int pitch64;               // shared-memory row pitch of the FP64 kernel (elements)
     int64_t N;
     const double *pts, *normals;
     const int64_t *row_ptr;
@@ -144,13 +144,17 @@ __device__ void reject_row(const WParams &P, int64_t row, int64_t rb, int n, int
     if (P.status && lane == 0) P.status[row] = st;
 }
 
-// Assemble [K | B] (FP64) into shared memory, row pitch `pitch`.  Returns the
-// warp-uniform max |K| over the A and Q blocks.
+// Assemble [K | B] (FP64) into shared memory, row pitch `pitch`.  The Q block
+// starts at row/column `qoff` >= n; rows and columns n .. qoff-1 are padding
+// (identity row and column, zero right-hand side), so a stencil of n nodes can
+// sit in a system laid out for qoff nodes.  The right-hand sides occupy
+// columns qoff + l .. qoff + l + R - 1.  Returns the warp-uniform max |K|
+// over the A and Q blocks.
 template <int DIM>
 __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const double *xi, double *K,
-                                int pitch) {
+                                int pitch, int qoff) {
     const int lane = threadIdx.x & 31;
-    const int l = P.l, M = n + l, k = P.k;
+    const int l = P.l, M = qoff + l, k = P.k;
     const int di = DIM - 2;
     double amax = 0.0;
     // A: unordered pairs (r, (r + d) mod n), d = 1 .. n/2, each once
@@ -172,20 +176,29 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
         }
     }
     for (int r = lane; r < n; r += 32) K[r * pitch + r] = 0.0;
+    // padding rows/columns n .. qoff-1: identity
+    for (int e = lane; e < (qoff - n) * (M + P.R); e += 32) {
+        int j = n + e / (M + P.R), c = e % (M + P.R);
+        K[j * pitch + c] = (c == j) ? 1.0 : 0.0;
+    }
+    for (int e = lane; e < (qoff - n) * M; e += 32) {
+        int j = n + e / M, r = e % M;
+        if (r < n || r >= qoff) K[r * pitch + j] = 0.0;
+    }
     // Q and Q^T: q_0 = 1, q_b = q_parent * xi_var
     for (int r = lane; r < n; r += 32) {
-        double *Kr = K + r * pitch + n;
+        double *Kr = K + r * pitch + qoff;
         Kr[0] = 1.0;
-        K[n * pitch + r] = 1.0;
+        K[qoff * pitch + r] = 1.0;
         for (int b = 1; b < l; ++b) {
             double v = Kr[c_mono.parent[di][b]] * xi[r * DIM + c_mono.var[di][b]];
             Kr[b] = v;
-            K[(n + b) * pitch + r] = v;
+            K[(qoff + b) * pitch + r] = v;
             amax = fmax(amax, fabs(v));
         }
     }
     amax = fmax(amax, 1.0);
-    for (int e = lane; e < l * l; e += 32) K[(n + e / l) * pitch + n + e % l] = 0.0;
+    for (int e = lane; e < l * l; e += 32) K[(qoff + e / l) * pitch + qoff + e % l] = 0.0;
     // right-hand sides in columns M .. M+R-1
     for (int j = lane; j < n; j += 32) {
         double r2 = 0.0;
@@ -226,7 +239,7 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
                     else v = (a == op - 1) ? 1.0 : 0.0;
                 }
             }
-            K[(n + b) * pitch + M + cI] = v;
+            K[(qoff + b) * pitch + M + cI] = v;
         }
     }
     __syncwarp();
@@ -331,7 +344,7 @@ __global__ void __launch_bounds__(128) k_weights_fp64(WParams P) {
             continue;
         }
         const int M = n + P.l;
-        double amax = assemble_fp64<DIM>(P, row, n, xi, K, P.pitch64);
+        double amax = assemble_fp64<DIM>(P, row, n, xi, K, P.pitch64, n);
         bool ok = lu_solve_fp64(K, P.pitch64, M, P.R, amax, invp, mul);
         if (!ok) {
             reject_row(P, row, rb, n, MM_ST_SINGULAR);
@@ -345,186 +358,301 @@ __global__ void __launch_bounds__(128) k_weights_fp64(WParams P) {
 }
 
 // ------------------------------------------------------------ mixed solver
-// FP32 LU with row partial pivoting in place (L below the diagonal, unit
-// diagonal implied; U on and above), perm[kk] = row swapped with kk,
-// invU[kk] = 1/U_kk.  Returns false on a pivot <= M * u32 * amax.
-__device__ bool lu_factor_fp32(float *A, int p, int M, float amax, int *perm, float *invU) {
+// FP32 LU with implicit partial pivoting: rows are never exchanged; the row
+// chosen at step kk is marked (step = kk) and copied to a per-warp buffer
+// from which the remaining rows are updated.  Lane t owns rows t, t+32, t+64
+// (RPL of them).  A32 [M x p32] (row-major, p32 odd) holds L below the pivots
+// and U in the pivot rows; A32[perm[kk]][kk] holds 1/U_kk.
+constexpr int kBig = 1 << 30;
+
+template <int RPL>
+__device__ bool lu32_implicit(float *A, int p32, int M, int *step, int *perm, float *ubuf,
+                              float tiny) {
     const int lane = threadIdx.x & 31;
-    const float tiny = (float)M * (FLT_EPSILON * 0.5f) * amax;
+    bool ok = true;
     for (int kk = 0; kk < M; ++kk) {
         float best = -1.0f;
-        int prow = M;
-        for (int r = kk + lane; r < M; r += 32) {
-            float v = fabsf(A[r * p + kk]);
-            if (v > best) { best = v; prow = r; }
+        int brow = kBig;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            if (step[q] == kBig) {
+                const int r = lane + 32 * q;
+                const float v = fabsf(A[r * p32 + kk]);
+                if (v > best) { best = v; brow = r; }
+            }
         }
+#pragma unroll
         for (int o = 16; o; o >>= 1) {
-            float ov = __shfl_xor_sync(kFull, best, o);
-            int orow = __shfl_xor_sync(kFull, prow, o);
-            if (ov > best || (ov == best && orow < prow)) { best = ov; prow = orow; }
+            const float ob = __shfl_xor_sync(kFull, best, o);
+            const int orow = __shfl_xor_sync(kFull, brow, o);
+            if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
         }
-        if (!(best > tiny)) return false;
-        if (lane == 0) perm[kk] = prow;
-        if (prow != kk) {
-            for (int c = lane; c < M; c += 32) {
-                float t = A[kk * p + c];
-                A[kk * p + c] = A[prow * p + c];
-                A[prow * p + c] = t;
-            }
-            __syncwarp();
-        }
-        float ip = 1.0f / A[kk * p + kk];
-        if (lane == 0) invU[kk] = ip;
-        for (int r = kk + 1 + lane; r < M; r += 32) A[r * p + kk] *= ip;
+        const bool good = best > tiny;
+        ok &= good;
+        if (brow == kBig) brow = 0;               // only when every row is exhausted (not reached)
+        const float *Up = A + brow * p32;
+        for (int c = kk + 1 + lane; c < M; c += 32) ubuf[c] = Up[c];
+        const float piv = Up[kk];
+        if (lane == 0) perm[kk] = brow;
         __syncwarp();
-        const int W = M - kk - 1, H = W;
-        if (H > 0) {
-            const int q32 = 32 / W, r32 = 32 % W;
-            int r = lane / W, c = lane % W;
-            for (; r < H;) {
-                float *dst = A + (kk + 1 + r) * p + kk + 1 + c;
-                *dst = fmaf(-A[(kk + 1 + r) * p + kk], A[kk * p + kk + 1 + c], *dst);
-                c += r32;
-                r += q32;
-                if (c >= W) { c -= W; ++r; }
+        const float ip = good ? 1.0f / piv : 0.0f;
+        float l[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            if (r == brow) { step[q] = kk; A[r * p32 + kk] = ip; }
+            l[q] = 0.0f;
+            if (step[q] == kBig) {
+                l[q] = A[r * p32 + kk] * ip;
+                A[r * p32 + kk] = l[q];
             }
         }
-        __syncwarp();
-    }
-    return true;
-}
-
-// Solve K y = b (trans = false) or K^T y = b (trans = true) in place for the
-// R columns of y [M x R] (row-major, FP32) with the factors above.
-__device__ void lu_solve_fp32(const float *A, int p, int M, const int *perm, const float *invU,
-                              float *y, int R, bool trans) {
-    const int lane = threadIdx.x & 31;
-    if (!trans) {
-        if (lane < R)
-            for (int kk = 0; kk < M; ++kk) {
-                int q = perm[kk];
-                if (q != kk) { float t = y[kk * R + lane]; y[kk * R + lane] = y[q * R + lane]; y[q * R + lane] = t; }
-            }
-        __syncwarp();
-        for (int kk = 0; kk < M - 1; ++kk) {             // L (unit lower)
-            for (int e = lane; e < (M - kk - 1) * R; e += 32) {
-                int r = kk + 1 + e / R, c = e % R;
-                y[r * R + c] = fmaf(-A[r * p + kk], y[kk * R + c], y[r * R + c]);
-            }
-            __syncwarp();
+        for (int c = kk + 1; c < M; ++c) {
+            const float u = ubuf[c];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q)
+                if (step[q] == kBig) {
+                    float *dst = A + (lane + 32 * q) * p32 + c;
+                    *dst = fmaf(-l[q], u, *dst);
+                }
         }
-        for (int kk = M - 1; kk >= 0; --kk) {            // U
-            if (lane < R) y[kk * R + lane] *= invU[kk];
-            __syncwarp();
-            for (int e = lane; e < kk * R; e += 32) {
-                int r = e / R, c = e % R;
-                y[r * R + c] = fmaf(-A[r * p + kk], y[kk * R + c], y[r * R + c]);
-            }
-            __syncwarp();
-        }
-    } else {
-        for (int kk = 0; kk < M; ++kk) {                 // U^T (lower)
-            if (lane < R) y[kk * R + lane] *= invU[kk];
-            __syncwarp();
-            for (int e = lane; e < (M - kk - 1) * R; e += 32) {
-                int r = kk + 1 + e / R, c = e % R;
-                y[r * R + c] = fmaf(-A[kk * p + r], y[kk * R + c], y[r * R + c]);
-            }
-            __syncwarp();
-        }
-        for (int kk = M - 1; kk > 0; --kk) {             // L^T (unit upper)
-            for (int e = lane; e < kk * R; e += 32) {
-                int r = e / R, c = e % R;
-                y[r * R + c] = fmaf(-A[kk * p + r], y[kk * R + c], y[r * R + c]);
-            }
-            __syncwarp();
-        }
-        if (lane < R)
-            for (int kk = M - 1; kk >= 0; --kk) {
-                int q = perm[kk];
-                if (q != kk) { float t = y[kk * R + lane]; y[kk * R + lane] = y[q * R + lane]; y[q * R + lane] = t; }
-            }
         __syncwarp();
     }
+    return ok;
 }
 
-// Estimate of ||K^-1||_1 from the FP32 factors: Hager's method with
-// Higham's refinements (at most `iters` power steps, plus the alternating
-// test vector).  v is an [M] scratch vector, w another.
-__device__ float inv_norm1_est(const float *A, int p, int M, const int *perm, const float *invU,
-                               float *v, int iters) {
+// Solve K x = b for R right-hand sides with the factors above.  z holds b
+// by row for the lane's own rows (consumed).  The solution x, by column, is
+// written to X [M x R] (shared) and returned after a warp barrier.
+template <int RPL, int R>
+__device__ void lu32_solve(const float *A, int p32, int M, const int *step, const int *perm,
+                           float (&z)[RPL][R], float *X) {
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i < M; i += 32) v[i] = 1.0f / M;
+    for (int kk = 0; kk < M; ++kk) {
+        const int p = perm[kk], owner = p & 31, qp = p >> 5;
+        float y[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            float v = z[0][c];
+#pragma unroll
+            for (int q = 1; q < RPL; ++q)
+                if (qp == q) v = z[q][c];
+            y[c] = __shfl_sync(kFull, v, owner);
+        }
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (step[q] > kk) {
+                const float a = A[(lane + 32 * q) * p32 + kk];
+#pragma unroll
+                for (int c = 0; c < R; ++c) z[q][c] = fmaf(-a, y[c], z[q][c]);
+            }
+    }
+    for (int kk = M - 1; kk >= 0; --kk) {
+        const int p = perm[kk], owner = p & 31, qp = p >> 5;
+        const float ip = A[p * p32 + kk];
+        float xk[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            float v = z[0][c];
+#pragma unroll
+            for (int q = 1; q < RPL; ++q)
+                if (qp == q) v = z[q][c];
+            xk[c] = __shfl_sync(kFull, v, owner) * ip;
+        }
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (step[q] >= 0 && step[q] < kk) {
+                const float a = A[(lane + 32 * q) * p32 + kk];
+#pragma unroll
+                for (int c = 0; c < R; ++c) z[q][c] = fmaf(-a, xk[c], z[q][c]);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < R; ++c) X[kk * R + c] = xk[c];
+    }
     __syncwarp();
+}
+
+// ||K^-1||_1 estimate from the factors (Hager's method with Higham's
+// refinements: a power step, one ascent step, the alternating-sign vector).
+// K is symmetric, so its transposed solves are plain solves.  X is [M] scratch.
+template <int RPL>
+__device__ float lu32_inv_norm1(const float *A, int p32, int M, const int *step, const int *perm,
+                                float *X) {
+    const int lane = threadIdx.x & 31;
+    float z[RPL][1];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) z[q][0] = 1.0f / M;
+    lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
     float est = 0.0f;
-    int jlast = -1;
-    for (int it = 0; it < iters; ++it) {
-        lu_solve_fp32(A, p, M, perm, invU, v, 1, false);      // v = K^-1 x
-        float s1 = 0.0f;
-        for (int i = lane; i < M; i += 32) s1 += fabsf(v[i]);
-        s1 = warp_sumf(s1);
-        if (it > 0 && s1 <= est) break;
-        est = s1;
-        __syncwarp();
-        for (int i = lane; i < M; i += 32) v[i] = v[i] >= 0.0f ? 1.0f : -1.0f;
-        __syncwarp();
-        lu_solve_fp32(A, p, M, perm, invU, v, 1, true);       // z = K^-T sign(v)
-        float zmax = -1.0f, zx = 0.0f;
-        int j = M;
-        for (int i = lane; i < M; i += 32) {
-            float a = fabsf(v[i]);
-            if (a > zmax) { zmax = a; j = i; }
-            zx += it == 0 ? v[i] / M : (i == jlast ? v[i] : 0.0f);   // z^T x
-        }
-        zx = warp_sumf(zx);
-        for (int o = 16; o; o >>= 1) {
-            float oz = __shfl_xor_sync(kFull, zmax, o);
-            int oj = __shfl_xor_sync(kFull, j, o);
-            if (oz > zmax || (oz == zmax && oj < j)) { zmax = oz; j = oj; }
-        }
-        if (zmax <= zx || j == jlast) break;   // no ascent direction left
-        jlast = j;
-        __syncwarp();
-        for (int i = lane; i < M; i += 32) v[i] = (i == j) ? 1.0f : 0.0f;
+    for (int i = lane; i < M; i += 32) est += fabsf(X[i]);
+    est = warp_sumf(est);
+    // z = K^-1 sign(x)
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+        z[q][0] = r < M ? (X[r] >= 0.0f ? 1.0f : -1.0f) : 0.0f;
+    }
+    __syncwarp();
+    lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
+    float zmax = -1.0f, zx = 0.0f;
+    int j = kBig;
+    for (int i = lane; i < M; i += 32) {
+        const float v = fabsf(X[i]);
+        if (v > zmax) { zmax = v; j = i; }
+        zx += X[i] / M;
+    }
+    zx = warp_sumf(zx);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float oz = __shfl_xor_sync(kFull, zmax, o);
+        const int oj = __shfl_xor_sync(kFull, j, o);
+        if (oz > zmax || (oz == zmax && oj < j)) { zmax = oz; j = oj; }
+    }
+    __syncwarp();
+    if (zmax > zx) {                      // ascent direction e_j
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) z[q][0] = (lane + 32 * q == j) ? 1.0f : 0.0f;
+        lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
+        float e2 = 0.0f;
+        for (int i = lane; i < M; i += 32) e2 += fabsf(X[i]);
+        est = fmaxf(est, warp_sumf(e2));
         __syncwarp();
     }
-    // alternating-sign vector, catches matrices where the power steps stall
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int i = lane + 32 * q;
+        z[q][0] = i < M ? ((i & 1) ? -1.0f : 1.0f) * (1.0f + (float)i / (float)max(M - 1, 1)) : 0.0f;
+    }
+    lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
+    float e3 = 0.0f;
+    for (int i = lane; i < M; i += 32) e3 += fabsf(X[i]);
+    e3 = warp_sumf(e3);
     __syncwarp();
-    for (int i = lane; i < M; i += 32)
-        v[i] = ((i & 1) ? -1.0f : 1.0f) * (1.0f + (float)i / (float)max(M - 1, 1));
-    __syncwarp();
-    lu_solve_fp32(A, p, M, perm, invU, v, 1, false);
-    float s2 = 0.0f;
-    for (int i = lane; i < M; i += 32) s2 += fabsf(v[i]);
-    s2 = warp_sumf(s2);
-    __syncwarp();
-    return fmaxf(est, 2.0f * s2 / (3.0f * M));
+    return fmaxf(est, 2.0f * e3 / (3.0f * M));
 }
 
-__host__ __device__ inline size_t mixed_warp_bytes(int M_max, int pitch64, int pitch32, int n_max,
-                                                    int dim, int R) {
-    size_t d = (size_t)M_max * pitch64 + (size_t)M_max * R + (size_t)n_max * dim;  // K64|b, x64, xi
-    size_t f = (size_t)M_max * pitch32 + (size_t)M_max * R + 2 * (size_t)M_max;    // K32, y32, invU, v
-    size_t i = (size_t)M_max;                                                       // perm
-    // every warp's block starts with FP64 data: keep the stride 16-byte aligned
-    return (d * 8 + f * 4 + i * 4 + 16 + 15) & ~size_t(15);
+// Per-warp shared memory of the mixed kernel (byte offsets, 16-aligned).
+struct MixedLayout {
+    int pA, p32;
+    size_t a64, q64, b64, x64, xi, a32, u32, v32, perm, bytes;
+};
+
+__host__ __device__ inline MixedLayout mixed_layout(int n_max, int l, int R, int dim) {
+    MixedLayout L{};
+    const int M = n_max + l;
+    L.pA = n_max | 1;
+    L.p32 = M | 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += (bytes + 15) & ~size_t(15);
+        return at;
+    };
+    L.a64 = take((size_t)n_max * L.pA * 8);
+    L.q64 = take((size_t)n_max * l * 8);
+    L.b64 = take((size_t)M * R * 8);
+    L.x64 = take((size_t)M * R * 8);
+    L.xi = take((size_t)n_max * dim * 8);
+    L.a32 = take((size_t)M * L.p32 * 4);
+    L.u32 = take((size_t)L.p32 * 4);
+    L.v32 = take((size_t)M * R * 4);
+    L.perm = take((size_t)M * 4);
+    L.bytes = o;
+    return L;
 }
 
+// Compact FP64 system for the residuals: A64 [n x pA] (diagonal 0), Q64
+// [n x l], B64 [M x R] (rows < n: l_phi, rows n + b: l_q).  Returns max |K|.
 template <int DIM>
+__device__ double assemble_mixed(const WParams &P, int64_t row, int n, const double *xi,
+                                 double *A64, int pA, double *Q64, double *B64, int R) {
+    const int lane = threadIdx.x & 31;
+    const int l = P.l, k = P.k, di = DIM - 2;
+    double amax = 0.0;
+    for (int d = 1; d <= n / 2; ++d) {
+        const int cnt = (2 * d == n) ? n / 2 : n;
+        for (int r = lane; r < cnt; r += 32) {
+            int c = r + d;
+            if (c >= n) c -= n;
+            double r2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const double t = xi[r * DIM + a] - xi[c * DIM + a];
+                r2 = fma(t, t, r2);
+            }
+            const double v = phs(r2, k);
+            A64[r * pA + c] = v;
+            A64[c * pA + r] = v;
+            amax = fmax(amax, v);
+        }
+    }
+    for (int r = lane; r < n; r += 32) {
+        A64[r * pA + r] = 0.0;
+        double *Qr = Q64 + r * l;
+        Qr[0] = 1.0;
+        for (int b = 1; b < l; ++b) {
+            const double v = Qr[c_mono.parent[di][b]] * xi[r * DIM + c_mono.var[di][b]];
+            Qr[b] = v;
+            amax = fmax(amax, fabs(v));
+        }
+        double r2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) r2 = fma(xi[r * DIM + a], xi[r * DIM + a], r2);
+        double rk2 = sqrt(r2);
+        for (int i = 3; i < k; i += 2) rk2 *= r2;
+        for (int cI = 0; cI < R; ++cI) {
+            const int op = P.opcode[cI];
+            double v;
+            if (op == 0) {
+                v = (double)(k * (k + DIM - 2)) * rk2;
+            } else {
+                double dot;
+                if (op == 4) {
+                    dot = 0.0;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) dot = fma(P.normals[row * DIM + a], xi[r * DIM + a], dot);
+                } else {
+                    dot = xi[r * DIM + (op - 1)];
+                }
+                v = -(double)k * rk2 * dot;
+            }
+            B64[r * R + cI] = v;
+        }
+    }
+    for (int b = lane; b < l; b += 32) {
+        for (int cI = 0; cI < R; ++cI) {
+            const int op = P.opcode[cI];
+            double v = 0.0;
+            if (op == 0) {
+                v = (double)c_mono.lap[di][b];
+            } else {
+                const int a = c_mono.lin[di][b];
+                if (a >= 0) v = op == 4 ? P.normals[row * DIM + a] : ((a == op - 1) ? 1.0 : 0.0);
+            }
+            B64[(n + b) * R + cI] = v;
+        }
+    }
+    __syncwarp();
+    return warp_max(fmax(amax, 1.0));
+}
+
+template <int DIM, int RPL, int R>
 __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int R = P.R;
-    char *base = (char *)smem + (size_t)wib * mixed_warp_bytes(P.M_max, P.pitch64, P.pitch32,
-                                                               P.n_max, DIM, R);
-    double *K64 = (double *)base;                       // [M_max x pitch64], B in cols M..
-    double *x64 = K64 + (size_t)P.M_max * P.pitch64;    // [M_max x R]
-    double *xi = x64 + (size_t)P.M_max * R;             // [n_max x DIM]
-    float *K32 = (float *)(xi + (size_t)P.n_max * DIM); // [M_max x pitch32]
-    float *y32 = K32 + (size_t)P.M_max * P.pitch32;     // [M_max x R]
-    float *invU = y32 + (size_t)P.M_max * R;
-    float *v32 = invU + P.M_max;
-    int *perm = (int *)(v32 + P.M_max);
+    const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
+    char *base = (char *)smem + (size_t)wib * Ly.bytes;
+    double *A64 = (double *)(base + Ly.a64);
+    double *Q64 = (double *)(base + Ly.q64);
+    double *B64 = (double *)(base + Ly.b64);
+    double *X64 = (double *)(base + Ly.x64);
+    double *xi = (double *)(base + Ly.xi);
+    float *A32 = (float *)(base + Ly.a32);
+    float *U32 = (float *)(base + Ly.u32);
+    float *V32 = (float *)(base + Ly.v32);
+    int *perm = (int *)(base + Ly.perm);
+    const int pA = Ly.pA, p32 = Ly.p32, l = P.l;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float u32 = FLT_EPSILON * 0.5f;
@@ -536,105 +664,163 @@ __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
             reject_row(P, row, rb, n, MM_ST_BADARG);
             continue;
         }
-        const int M = n + P.l, p64 = P.pitch64, p32 = P.pitch32;
-        double amax = assemble_fp64<DIM>(P, row, n, xi, K64, p64);
-        // FP32 copy and its 1-norm
-        float cmax = 0.0f;
-        for (int c = lane; c < M; c += 32) {
-            float cs = 0.0f;
-            for (int r = 0; r < M; ++r) {
-                float v = (float)K64[r * p64 + c];
-                K32[r * p32 + c] = v;
-                cs += fabsf(v);
+        const int M = n + l;
+        const double amax = assemble_mixed<DIM>(P, row, n, xi, A64, pA, Q64, B64, R);
+        // FP32 copy fl32(K64), row by row (own rows), and ||K||_1 (= max row sum)
+        int step[RPL];
+        float n1 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            step[q] = r < M ? kBig : -1;
+            if (r < M) {
+                float *Ar = A32 + r * p32;
+                float rs = 0.0f;
+                if (r < n) {
+                    for (int c = 0; c < n; ++c) { const float v = (float)A64[r * pA + c]; Ar[c] = v; rs += fabsf(v); }
+                    for (int b = 0; b < l; ++b) { const float v = (float)Q64[r * l + b]; Ar[n + b] = v; rs += fabsf(v); }
+                } else {
+                    const int b = r - n;
+                    for (int c = 0; c < n; ++c) { const float v = (float)Q64[c * l + b]; Ar[c] = v; rs += fabsf(v); }
+                    for (int c = n; c < M; ++c) Ar[c] = 0.0f;
+                }
+                n1 = fmaxf(n1, rs);
             }
-            cmax = fmaxf(cmax, cs);
         }
-        float norm1 = warp_maxf(cmax);
+        n1 = warp_maxf(n1);
         __syncwarp();
-        bool queue = !lu_factor_fp32(K32, p32, M, (float)amax, perm, invU);
+        bool queue = !lu32_implicit<RPL>(A32, p32, M, step, perm, U32, (float)M * u32 * (float)amax);
         if (!queue) {
-            float kest = norm1 * inv_norm1_est(K32, p32, M, perm, invU, v32, 3);
+            const float kest = n1 * lu32_inv_norm1<RPL>(A32, p32, M, step, perm, V32);
             queue = !((double)kest * u32 <= P.kappa_max);
         }
         bool conv = false;
         if (!queue) {
-            // x = 0, r = b; refine: y = K32^-1 r; x += y; r = b - K64 x (FP64)
-            for (int e = lane; e < M * R; e += 32) {
-                int r = e / R, c = e - r * R;
-                x64[e] = 0.0;
-                y32[e] = (float)K64[r * p64 + M + c];
+            float z[RPL][R];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int r = lane + 32 * q;
+#pragma unroll
+                for (int c = 0; c < R; ++c) z[q][c] = r < M ? (float)B64[r * R + c] : 0.0f;
             }
-            __syncwarp();
             double dprev = 0.0;
-            for (int step = 0; step <= P.ir_max_steps; ++step) {
-                lu_solve_fp32(K32, p32, M, perm, invU, y32, R, false);
+            for (int it = 0; it <= P.ir_max_steps; ++it) {
+                lu32_solve<RPL, R>(A32, p32, M, step, perm, z, V32);
                 double dmax = 0.0, xmax = 0.0;
                 for (int e = lane; e < M * R; e += 32) {
-                    double d = (double)y32[e];
-                    double xn = x64[e] + d;
-                    x64[e] = xn;
+                    const double d = (double)V32[e];
+                    const double xn = (it == 0 ? 0.0 : X64[e]) + d;
+                    X64[e] = xn;
                     dmax = fmax(dmax, fabs(d));
                     if (e < n * R) xmax = fmax(xmax, fabs(xn));
                 }
                 dmax = warp_max(dmax);
                 xmax = warp_max(xmax);
-                if (step > 0) {
-                    // observed contraction of the last step bounds the error left
-                    double theta = dmax / fmax(dprev, 1e-300);
+                if (it > 0) {
+                    // the observed contraction of the last step bounds the error left
+                    const double theta = dmax / fmax(dprev, 1e-300);
                     if (theta < 0.5 && theta / (1.0 - theta) * dmax <= P.ir_tol * xmax) {
                         conv = true;
                         break;
                     }
                 }
-                if (step == P.ir_max_steps) break;
+                if (it == P.ir_max_steps) break;
                 dprev = dmax;
                 __syncwarp();
-                // FP64 residual r = b - K64 x (skipping the zero block), rounded to FP32
+                // FP64 residual b - K64 x over the nonzero blocks
                 for (int e = lane; e < M * R; e += 32) {
-                    int i = e / R, c = e - i * R;
-                    const double *Ki = K64 + i * p64;
-                    double acc = Ki[M + c];
-                    int jend = i < n ? M : n;
-                    for (int j = 0; j < jend; ++j) acc = fma(-Ki[j], x64[j * R + c], acc);
-                    y32[e] = (float)acc;
+                    const int i = e / R, c = e - i * R;
+                    double acc = B64[e];
+                    if (i < n) {
+                        const double *Ai = A64 + i * pA;
+                        const double *Qi = Q64 + i * l;
+                        for (int j = 0; j < n; ++j) acc = fma(-Ai[j], X64[j * R + c], acc);
+                        for (int b = 0; b < l; ++b) acc = fma(-Qi[b], X64[(n + b) * R + c], acc);
+                    } else {
+                        const int b = i - n;
+                        for (int j = 0; j < n; ++j) acc = fma(-Q64[j * l + b], X64[j * R + c], acc);
+                    }
+                    V32[e] = (float)acc;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int r = lane + 32 * q;
+#pragma unroll
+                    for (int c = 0; c < R; ++c) z[q][c] = r < M ? V32[r * R + c] : 0.0f;
                 }
                 __syncwarp();
             }
-        }
-        if (conv) {
-            // Constraint rows: one more FP64 residual on Q^T w = l_q only (A rows
-            // taken as satisfied), corrected through the FP32 factors, so the
-            // monomials are reproduced to FP64 rounding rather than to the
-            // refinement tolerance.
-            for (int e = lane; e < M * R; e += 32) {
-                int i = e / R, c = e - i * R;
-                float rv = 0.0f;
-                if (i >= n) {
-                    const double *Ki = K64 + i * p64;
-                    double acc = Ki[M + c];
-                    for (int j = 0; j < n; ++j) acc = fma(-Ki[j], x64[j * R + c], acc);
-                    rv = (float)acc;
+            if (conv) {
+                // Constraint rows Q^T w = l_q: one more FP64 residual on those rows
+                // only, corrected through the FP32 factors, so the monomials are
+                // reproduced to FP64 rounding rather than to the refinement tolerance.
+                __syncwarp();
+                for (int e = lane; e < l * R; e += 32) {
+                    const int b = e / R, c = e - b * R;
+                    double acc = B64[(n + b) * R + c];
+                    for (int j = 0; j < n; ++j) acc = fma(-Q64[j * l + b], X64[j * R + c], acc);
+                    V32[e] = (float)acc;
                 }
-                y32[e] = rv;
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int r = lane + 32 * q;
+#pragma unroll
+                    for (int c = 0; c < R; ++c) z[q][c] = (r >= n && r < M) ? V32[(r - n) * R + c] : 0.0f;
+                }
+                __syncwarp();
+                lu32_solve<RPL, R>(A32, p32, M, step, perm, z, V32);
+                for (int e = lane; e < n * R; e += 32) X64[e] += (double)V32[e];
+                __syncwarp();
             }
-            __syncwarp();
-            lu_solve_fp32(K32, p32, M, perm, invU, y32, R, false);
-            for (int e = lane; e < M * R; e += 32) x64[e] += (double)y32[e];
-            __syncwarp();
         }
         if (!conv) {
             if (lane == 0) {
-                int slot = atomicAdd(P.fb_count, 1);
+                const int slot = atomicAdd(P.fb_count, 1);
                 P.fb_list[slot] = (int)row;
                 if (P.status) P.status[row] = MM_ST_NONCONVERGED;
             }
             __syncwarp();
             continue;
         }
-        store_weights(P, rb, n, s, x64, R, 0);
+        store_weights(P, rb, n, s, X64, R, 0);
         if (P.status && lane == 0) P.status[row] = MM_ST_OK;
         __syncwarp();
     }
+}
+
+template <int DIM, int RPL, int R>
+int launch_mixed_t(mm_ctx *ctx, const WParams &P, int64_t rows) {
+    const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
+    auto kern = k_weights_mixed<DIM, RPL, R>;
+    int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / Ly.bytes));
+    const size_t sm = Ly.bytes * wpb;
+    if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "stencil too large for shared memory");
+    MM_CUDA_CHECK(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int blocks = (int)std::min<int64_t>((rows + wpb - 1) / wpb, (int64_t)ctx->num_sms * 32);
+    kern<<<blocks, wpb * 32, sm, ctx->stream>>>(P);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+template <int DIM, int RPL>
+int launch_mixed_r(mm_ctx *ctx, const WParams &P, int64_t rows) {
+    switch (P.R) {
+        case 1: return launch_mixed_t<DIM, RPL, 1>(ctx, P, rows);
+        case 2: return launch_mixed_t<DIM, RPL, 2>(ctx, P, rows);
+        case 3: return launch_mixed_t<DIM, RPL, 3>(ctx, P, rows);
+        case 4: return launch_mixed_t<DIM, RPL, 4>(ctx, P, rows);
+        default: return launch_mixed_t<DIM, RPL, 5>(ctx, P, rows);
+    }
+}
+
+template <int DIM>
+int launch_mixed(mm_ctx *ctx, const WParams &P, int64_t rows) {
+    const int rpl = (P.M_max + 31) / 32;
+    if (rpl <= 1) return launch_mixed_r<DIM, 1>(ctx, P, rows);
+    if (rpl == 2) return launch_mixed_r<DIM, 2>(ctx, P, rows);
+    return launch_mixed_r<DIM, 3>(ctx, P, rows);
 }
 
 // ------------------------------------------------------------- host side
@@ -727,7 +913,6 @@ int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, in
         }
     P.R = R;
     P.pitch64 = (P.M_max + R) | 1;
-    P.pitch32 = P.M_max | 1;
     P.ir_tol = ctx->ir_tol;
     P.ir_max_steps = ctx->ir_max_steps;
     P.kappa_max = ctx->kappa_max;
@@ -775,19 +960,10 @@ int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, in
         P.fb_list = (int *)(ws + o_list);
     }
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(P.fb_count, 0, sizeof(int), st));
-    const size_t wm = mixed_warp_bytes(P.M_max, P.pitch64, P.pitch32, P.n_max, dim, R);
-    int wpb = warps_for(wm);
-    size_t sm = wm * wpb;
-    if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "stencil too large for shared memory");
-    int blocks = (int)std::min<int64_t>((rows + wpb - 1) / wpb, (int64_t)ctx->num_sms * 32);
-    if (dim == 2) {
-        MM_CUDA_CHECK(ctx, cudaFuncSetAttribute(k_weights_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_weights_mixed<2><<<blocks, wpb * 32, sm, st>>>(P);
-    } else {
-        MM_CUDA_CHECK(ctx, cudaFuncSetAttribute(k_weights_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_weights_mixed<3><<<blocks, wpb * 32, sm, st>>>(P);
+    {
+        const int rc = dim == 2 ? launch_mixed<2>(ctx, P, rows) : launch_mixed<3>(ctx, P, rows);
+        if (rc != MM_OK) return rc;
     }
-    MM_LAUNCH_CHECK(ctx);
     return launch_fp64(P.fb_list, P.fb_count, rows);
 }
 
