@@ -390,8 +390,11 @@ __device__ bool lu32_implicit(float *A, int p32, int M, int *step, int *perm, fl
         const bool good = best > tiny;
         ok &= good;
         if (brow == kBig) brow = 0;               // only when every row is exhausted (not reached)
+        // pivot row from the even column c0 <= kk+1 on, zeros at columns <= kk, so
+        // the updates below can run on column pairs
+        const int c0 = (kk + 1) & ~1;
         const float *Up = A + brow * p32;
-        for (int c = kk + 1 + lane; c < M; c += 32) ubuf[c] = Up[c];
+        for (int c = c0 + lane; c < p32; c += 32) ubuf[c] = (c > kk && c < M) ? Up[c] : 0.0f;
         const float piv = Up[kk];
         if (lane == 0) perm[kk] = brow;
         __syncwarp();
@@ -407,13 +410,18 @@ __device__ bool lu32_implicit(float *A, int p32, int M, int *step, int *perm, fl
                 A[r * p32 + kk] = l[q];
             }
         }
-        for (int c = kk + 1; c < M; ++c) {
-            const float u = ubuf[c];
+        __syncwarp();
+        const float2 *u2 = reinterpret_cast<const float2 *>(ubuf);
+        for (int c = c0; c < M; c += 2) {
+            const float2 u = u2[c >> 1];
 #pragma unroll
             for (int q = 0; q < RPL; ++q)
                 if (step[q] == kBig) {
-                    float *dst = A + (lane + 32 * q) * p32 + c;
-                    *dst = fmaf(-l[q], u, *dst);
+                    float2 *dst = reinterpret_cast<float2 *>(A + (lane + 32 * q) * p32 + c);
+                    float2 a = *dst;
+                    a.x = fmaf(-l[q], u.x, a.x);
+                    a.y = fmaf(-l[q], u.y, a.y);
+                    *dst = a;
                 }
         }
         __syncwarp();
@@ -473,65 +481,6 @@ __device__ void lu32_solve(const float *A, int p32, int M, const int *step, cons
     __syncwarp();
 }
 
-// ||K^-1||_1 estimate from the factors (Hager's method with Higham's
-// refinements: a power step, one ascent step, the alternating-sign vector).
-// K is symmetric, so its transposed solves are plain solves.  X is [M] scratch.
-template <int RPL>
-__device__ float lu32_inv_norm1(const float *A, int p32, int M, const int *step, const int *perm,
-                                float *X) {
-    const int lane = threadIdx.x & 31;
-    float z[RPL][1];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) z[q][0] = 1.0f / M;
-    lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
-    float est = 0.0f;
-    for (int i = lane; i < M; i += 32) est += fabsf(X[i]);
-    est = warp_sumf(est);
-    // z = K^-1 sign(x)
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int r = lane + 32 * q;
-        z[q][0] = r < M ? (X[r] >= 0.0f ? 1.0f : -1.0f) : 0.0f;
-    }
-    __syncwarp();
-    lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
-    float zmax = -1.0f, zx = 0.0f;
-    int j = kBig;
-    for (int i = lane; i < M; i += 32) {
-        const float v = fabsf(X[i]);
-        if (v > zmax) { zmax = v; j = i; }
-        zx += X[i] / M;
-    }
-    zx = warp_sumf(zx);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float oz = __shfl_xor_sync(kFull, zmax, o);
-        const int oj = __shfl_xor_sync(kFull, j, o);
-        if (oz > zmax || (oz == zmax && oj < j)) { zmax = oz; j = oj; }
-    }
-    __syncwarp();
-    if (zmax > zx) {                      // ascent direction e_j
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) z[q][0] = (lane + 32 * q == j) ? 1.0f : 0.0f;
-        lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
-        float e2 = 0.0f;
-        for (int i = lane; i < M; i += 32) e2 += fabsf(X[i]);
-        est = fmaxf(est, warp_sumf(e2));
-        __syncwarp();
-    }
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int i = lane + 32 * q;
-        z[q][0] = i < M ? ((i & 1) ? -1.0f : 1.0f) * (1.0f + (float)i / (float)max(M - 1, 1)) : 0.0f;
-    }
-    lu32_solve<RPL, 1>(A, p32, M, step, perm, z, X);
-    float e3 = 0.0f;
-    for (int i = lane; i < M; i += 32) e3 += fabsf(X[i]);
-    e3 = warp_sumf(e3);
-    __syncwarp();
-    return fmaxf(est, 2.0f * e3 / (3.0f * M));
-}
-
 // Per-warp shared memory of the mixed kernel (byte offsets, 16-aligned).
 struct MixedLayout {
     int pA, p32;
@@ -542,7 +491,8 @@ __host__ __device__ inline MixedLayout mixed_layout(int n_max, int l, int R, int
     MixedLayout L{};
     const int M = n_max + l;
     L.pA = n_max | 1;
-    L.p32 = M | 1;
+    L.p32 = ((M + 1) & ~1) | 2;        // 2 * odd: float2 rows, few column conflicts
+    if (L.p32 < M) L.p32 += 4;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -556,7 +506,7 @@ __host__ __device__ inline MixedLayout mixed_layout(int n_max, int l, int R, int
     L.xi = take((size_t)n_max * dim * 8);
     L.a32 = take((size_t)M * L.p32 * 4);
     L.u32 = take((size_t)L.p32 * 4);
-    L.v32 = take((size_t)M * R * 4);
+    L.v32 = take((size_t)M * (R + 1) * 4);
     L.perm = take((size_t)M * 4);
     L.bytes = o;
     return L;
@@ -666,67 +616,81 @@ __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
         }
         const int M = n + l;
         const double amax = assemble_mixed<DIM>(P, row, n, xi, A64, pA, Q64, B64, R);
-        // FP32 copy fl32(K64), row by row (own rows), and ||K||_1 (= max row sum)
+        // FP32 system: the A block as fl32 of the FP64 one, Q and Q^T from the
+        // FP32 offsets (own rows; Q^T entries written by the row's owner)
         int step[RPL];
-        float n1 = 0.0f;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             const int r = lane + 32 * q;
             step[q] = r < M ? kBig : -1;
-            if (r < M) {
+            if (r < n) {
                 float *Ar = A32 + r * p32;
-                float rs = 0.0f;
-                if (r < n) {
-                    for (int c = 0; c < n; ++c) { const float v = (float)A64[r * pA + c]; Ar[c] = v; rs += fabsf(v); }
-                    for (int b = 0; b < l; ++b) { const float v = (float)Q64[r * l + b]; Ar[n + b] = v; rs += fabsf(v); }
-                } else {
-                    const int b = r - n;
-                    for (int c = 0; c < n; ++c) { const float v = (float)Q64[c * l + b]; Ar[c] = v; rs += fabsf(v); }
-                    for (int c = n; c < M; ++c) Ar[c] = 0.0f;
+                for (int c = 0; c < n; ++c) Ar[c] = (float)A64[r * pA + c];
+                float x32[DIM];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) x32[d] = (float)xi[r * DIM + d];
+                float *Qr = Ar + n;
+                Qr[0] = 1.0f;
+                A32[n * p32 + r] = 1.0f;
+                for (int b = 1; b < l; ++b) {
+                    const float v = Qr[c_mono.parent[DIM - 2][b]] * x32[c_mono.var[DIM - 2][b]];
+                    Qr[b] = v;
+                    A32[(n + b) * p32 + r] = v;
                 }
+            } else if (r < M) {
+                for (int c = n; c < M; ++c) A32[r * p32 + c] = 0.0f;
+            }
+        }
+        __syncwarp();
+        float n1 = 0.0f;   // ||K||_1 = max row sum (symmetric)
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            if (r < M) {
+                float rs = 0.0f;
+                for (int c = 0; c < M; ++c) rs += fabsf(A32[r * p32 + c]);
                 n1 = fmaxf(n1, rs);
             }
         }
         n1 = warp_maxf(n1);
-        __syncwarp();
         bool queue = !lu32_implicit<RPL>(A32, p32, M, step, perm, U32, (float)M * u32 * (float)amax);
-        if (!queue) {
-            const float kest = n1 * lu32_inv_norm1<RPL>(A32, p32, M, step, perm, V32);
-            queue = !((double)kest * u32 <= P.kappa_max);
-        }
         bool conv = false;
         if (!queue) {
-            float z[RPL][R];
+            // Refinement.  The first two solves carry one extra column: a step of
+            // Hager's 1-norm estimator of K^-1 (y = K^-1 e/M, then z = K^-T sign(y),
+            // est = max(||y||_1, ||z||_inf); K is symmetric), which gates the
+            // stencil to the FP64 solve if est * ||K||_1 * u32 is too large.
+            constexpr int RC = R + 1;
+            float z[RPL][RC];
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
                 const int r = lane + 32 * q;
 #pragma unroll
                 for (int c = 0; c < R; ++c) z[q][c] = r < M ? (float)B64[r * R + c] : 0.0f;
+                z[q][R] = r < M ? 1.0f / M : 0.0f;
             }
-            double dprev = 0.0;
-            for (int it = 0; it <= P.ir_max_steps; ++it) {
-                lu32_solve<RPL, R>(A32, p32, M, step, perm, z, V32);
-                double dmax = 0.0, xmax = 0.0;
-                for (int e = lane; e < M * R; e += 32) {
-                    const double d = (double)V32[e];
-                    const double xn = (it == 0 ? 0.0 : X64[e]) + d;
-                    X64[e] = xn;
+            lu32_solve<RPL, RC>(A32, p32, M, step, perm, z, V32);
+            float est = 0.0f;
+            double dmax = 0.0;
+            for (int i = lane; i < M; i += 32) {
+                est += fabsf(V32[i * RC + R]);
+#pragma unroll
+                for (int c = 0; c < R; ++c) {
+                    const double d = (double)V32[i * RC + c];
+                    X64[i * R + c] = d;
                     dmax = fmax(dmax, fabs(d));
-                    if (e < n * R) xmax = fmax(xmax, fabs(xn));
                 }
-                dmax = warp_max(dmax);
-                xmax = warp_max(xmax);
-                if (it > 0) {
-                    // the observed contraction of the last step bounds the error left
-                    const double theta = dmax / fmax(dprev, 1e-300);
-                    if (theta < 0.5 && theta / (1.0 - theta) * dmax <= P.ir_tol * xmax) {
-                        conv = true;
-                        break;
-                    }
-                }
-                if (it == P.ir_max_steps) break;
-                dprev = dmax;
-                __syncwarp();
+            }
+            est = warp_sumf(est);
+            double dprev = warp_max(dmax);
+            float sg[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int r = lane + 32 * q;
+                sg[q] = r < M ? (V32[r * RC + R] >= 0.0f ? 1.0f : -1.0f) : 0.0f;
+            }
+            __syncwarp();
+            for (int it = 1; it <= P.ir_max_steps; ++it) {
                 // FP64 residual b - K64 x over the nonzero blocks
                 for (int e = lane; e < M * R; e += 32) {
                     const int i = e / R, c = e - i * R;
@@ -743,12 +707,59 @@ __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
                     V32[e] = (float)acc;
                 }
                 __syncwarp();
+                double dmx = 0.0, xmax = 0.0;
+                if (it == 1) {
 #pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const int r = lane + 32 * q;
+                    for (int q = 0; q < RPL; ++q) {
+                        const int r = lane + 32 * q;
 #pragma unroll
-                    for (int c = 0; c < R; ++c) z[q][c] = r < M ? V32[r * R + c] : 0.0f;
+                        for (int c = 0; c < R; ++c) z[q][c] = r < M ? V32[r * R + c] : 0.0f;
+                        z[q][R] = sg[q];
+                    }
+                    __syncwarp();
+                    lu32_solve<RPL, RC>(A32, p32, M, step, perm, z, V32);
+                    float zinf = 0.0f;
+                    for (int i = lane; i < M; i += 32) {
+                        zinf = fmaxf(zinf, fabsf(V32[i * RC + R]));
+#pragma unroll
+                        for (int c = 0; c < R; ++c) {
+                            const double d = (double)V32[i * RC + c];
+                            const double xn = X64[i * R + c] + d;
+                            X64[i * R + c] = xn;
+                            dmx = fmax(dmx, fabs(d));
+                            if (i < n) xmax = fmax(xmax, fabs(xn));
+                        }
+                    }
+                    zinf = warp_maxf(zinf);
+                    const float kest = n1 * fmaxf(est, zinf);
+                    if (!((double)kest * u32 <= P.kappa_max)) { queue = true; break; }
+                } else {
+                    float zr[RPL][R];
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        const int r = lane + 32 * q;
+#pragma unroll
+                        for (int c = 0; c < R; ++c) zr[q][c] = r < M ? V32[r * R + c] : 0.0f;
+                    }
+                    __syncwarp();
+                    lu32_solve<RPL, R>(A32, p32, M, step, perm, zr, V32);
+                    for (int e = lane; e < M * R; e += 32) {
+                        const double d = (double)V32[e];
+                        const double xn = X64[e] + d;
+                        X64[e] = xn;
+                        dmx = fmax(dmx, fabs(d));
+                        if (e < n * R) xmax = fmax(xmax, fabs(xn));
+                    }
                 }
+                dmx = warp_max(dmx);
+                xmax = warp_max(xmax);
+                // the observed contraction of the last step bounds the error left
+                const double theta = dmx / fmax(dprev, 1e-300);
+                if (theta < 0.5 && theta / (1.0 - theta) * dmx <= P.ir_tol * xmax) {
+                    conv = true;
+                    break;
+                }
+                dprev = dmx;
                 __syncwarp();
             }
             if (conv) {
@@ -763,14 +774,15 @@ __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
                     V32[e] = (float)acc;
                 }
                 __syncwarp();
+                float zr[RPL][R];
 #pragma unroll
                 for (int q = 0; q < RPL; ++q) {
                     const int r = lane + 32 * q;
 #pragma unroll
-                    for (int c = 0; c < R; ++c) z[q][c] = (r >= n && r < M) ? V32[(r - n) * R + c] : 0.0f;
+                    for (int c = 0; c < R; ++c) zr[q][c] = (r >= n && r < M) ? V32[(r - n) * R + c] : 0.0f;
                 }
                 __syncwarp();
-                lu32_solve<RPL, R>(A32, p32, M, step, perm, z, V32);
+                lu32_solve<RPL, R>(A32, p32, M, step, perm, zr, V32);
                 for (int e = lane; e < n * R; e += 32) X64[e] += (double)V32[e];
                 __syncwarp();
             }
