@@ -5,6 +5,14 @@
 // computed in FP64 exactly as sum_a (p_a - c_a)^2 in dimension order with
 // round-to-nearest and no fused multiply-add (__dsub_rn/__dmul_rn/__dadd_rn),
 // so any exact implementation of the same ranking gives bit-identical rows.
+// Keys are compared as integers: for d2 >= 0 the IEEE bit pattern orders like
+// the value, so the top list needs no FP64 compare.
+//
+// FP64 is scarce on this GPU, so everything that only has to be conservative
+// runs in FP32 with an explicit error bound delta on FP32 distances (from the
+// largest coordinate magnitude): cell pruning, the stop test, and a candidate
+// filter that rejects a node when even its distance minus delta cannot beat
+// the current n-th best.  Only candidates that pass get the exact FP64 key.
 //
 // Two search strategies, one warp per query, both exact:
 //  * grid: nodes are counting-sorted into a uniform grid (cell edge chosen
@@ -33,6 +41,9 @@ struct GridParams {
     double inv_cell;
     int dims[3];
     int ncells;
+    float lo32[3];     // FP32 copies for the conservative tests
+    float cell32;
+    float delta32;     // bound on |FP32 distance - exact distance| for any two nodes
 };
 
 // ------------------------------------------------------------------ binning
@@ -116,6 +127,13 @@ __global__ void k_grid_params(const double *partial, int nparts, int64_t N, doub
     }
     gp->cell = c;
     gp->inv_cell = 1.0 / c;
+    double amax = 0.0;
+    for (int a = 0; a < DIM; ++a) amax = fmax(amax, fmax(fabs(lo[a]), fabs(hi[a])));
+    for (int a = 0; a < 3; ++a) gp->lo32[a] = (float)gp->lo[a];
+    gp->cell32 = (float)c;
+    // each coordinate rounds by <= u32*amax, the difference by <= 2*u32*amax,
+    // the FP32 square, sum and root by a few u32 of the distance (<= 2*amax*sqrt(d))
+    gp->delta32 = (float)(16.0 * (FLT_EPSILON * 0.5) * amax * sqrt((double)DIM)) + 1e-30f;
     long long nc = 1;
     for (int a = 0; a < DIM; ++a) nc *= dims[a];
     gp->ncells = (int)nc;
@@ -213,57 +231,80 @@ __global__ void k_scan_add(const int *tile_sum, const GridParams *gp, int *start
 
 template <int DIM>
 __global__ void k_scatter(const double *__restrict__ pts, int64_t N, const int *cell_of,
-                          const int *rank, const int *start, double *spts, int *sidx) {
+                          const int *rank, const int *start, double *spts, float *spts32,
+                          int *sidx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int d = start[cell_of[i]] + rank[i];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) spts[(int64_t)d * DIM + a] = pts[i * DIM + a];
+        for (int a = 0; a < DIM; ++a) {
+            const double v = pts[i * DIM + a];
+            spts[(int64_t)d * DIM + a] = v;
+            spts32[(int64_t)d * DIM + a] = (float)v;
+        }
         sidx[d] = (int)i;
     }
 }
 
+template <int DIM>
+__global__ void k_to_fp32(const double *__restrict__ pts, int64_t N, float *pts32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N * DIM;
+         i += (int64_t)gridDim.x * blockDim.x)
+        pts32[i] = (float)pts[i];
+}
+
+// Delta for the brute-force search (no grid): from the largest coordinate.
+template <int DIM>
+__global__ void k_brute_delta(const double *partial, int nparts, float *delta) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double amax = 0.0;
+    for (int j = 0; j < nparts * 2 * DIM; ++j) amax = fmax(amax, fabs(partial[j]));
+    *delta = (float)(16.0 * (FLT_EPSILON * 0.5) * amax * sqrt((double)DIM)) + 1e-30f;
+}
+
 // ------------------------------------------------------------- the top list
-__device__ __forceinline__ bool key_lt(double da, int ia, double db, int ib) {
+typedef unsigned long long u64;
+constexpr u64 kInfBits = 0x7ff0000000000000ULL;    // +inf: empty slot
+
+__device__ __forceinline__ bool key_lt(u64 da, int ia, u64 db, int ib) {
     return da < db || (da == db && ia < ib);
 }
 
-// Sorted list of the K best (d2, index) keys; slot s on lane s (lo) and on
-// lane s-32 (hi).  Empty slots hold (+inf, INT_MAX).
+// Sorted list of the K best (d2 bits, index) keys; slot s on lane s (lo) and
+// on lane s-32 (hi).  Empty slots hold (+inf, INT_MAX).
 struct TopList {
-    double dlo, dhi;
+    u64 dlo, dhi;
     int ilo, ihi;
     int K;
 
     __device__ void init(int k) {
         K = k;
-        dlo = dhi = __longlong_as_double(0x7ff0000000000000LL);
+        dlo = dhi = kInfBits;
         ilo = ihi = 0x7fffffff;
     }
     // Key of slot K-1 (the worst kept), broadcast to all lanes.
-    __device__ void worst(double &d, int &i) const {
-        if (K == 0) { d = -1.0; i = -1; return; }
-        int s = K - 1;
-        int src = s & 31;
-        double dv = s < 32 ? dlo : dhi;
-        int iv = s < 32 ? ilo : ihi;
+    __device__ void worst(u64 &d, int &i) const {
+        if (K == 0) { d = 0; i = -1; return; }
+        const int s = K - 1, src = s & 31;
+        const u64 dv = s < 32 ? dlo : dhi;
+        const int iv = s < 32 ? ilo : ihi;
         d = __shfl_sync(kFull, dv, src);
         i = __shfl_sync(kFull, iv, src);
     }
     // Insert a warp-uniform key known to be better than the worst.
-    __device__ void insert(double d, int idx) {
-        int lane = threadIdx.x & 31;
-        unsigned blo = __ballot_sync(kFull, key_lt(dlo, ilo, d, idx));
-        unsigned bhi = __ballot_sync(kFull, key_lt(dhi, ihi, d, idx));
-        int pos = __popc(blo) + __popc(bhi);
-        double pdlo = __shfl_up_sync(kFull, dlo, 1);
-        int pilo = __shfl_up_sync(kFull, ilo, 1);
-        double pdhi = __shfl_up_sync(kFull, dhi, 1);
+    __device__ void insert(u64 d, int idx) {
+        const int lane = threadIdx.x & 31;
+        const unsigned blo = __ballot_sync(kFull, key_lt(dlo, ilo, d, idx));
+        const unsigned bhi = __ballot_sync(kFull, key_lt(dhi, ihi, d, idx));
+        const int pos = __popc(blo) + __popc(bhi);
+        const u64 pdlo = __shfl_up_sync(kFull, dlo, 1);
+        const int pilo = __shfl_up_sync(kFull, ilo, 1);
+        u64 pdhi = __shfl_up_sync(kFull, dhi, 1);
         int pihi = __shfl_up_sync(kFull, ihi, 1);
-        double d31 = __shfl_sync(kFull, dlo, 31);
-        int i31 = __shfl_sync(kFull, ilo, 31);
+        const u64 d31 = __shfl_sync(kFull, dlo, 31);
+        const int i31 = __shfl_sync(kFull, ilo, 31);
         if (lane == 0) { pdhi = d31; pihi = i31; }
-        int slo = lane, shi = lane + 32;
+        const int slo = lane, shi = lane + 32;
         if (shi > pos) { dhi = pdhi; ihi = pihi; }
         if (shi == pos) { dhi = d; ihi = idx; }
         if (slo > pos) { dlo = pdlo; ilo = pilo; }
@@ -283,18 +324,45 @@ __device__ __forceinline__ double dist2_rn(const double *p, const double *c) {
     return s;
 }
 
-// Offer one candidate per lane (valid lanes only); inserts those that beat the
-// current worst, best-first order not required.
-__device__ __forceinline__ void offer(TopList &tl, bool valid, double d, int idx, double &wd,
-                                      int &wi) {
-    unsigned m = __ballot_sync(kFull, valid && key_lt(d, idx, wd, wi));
+// Worst key as an FP32 upper bound of its squared distance (inf while the list
+// is not full).
+__device__ __forceinline__ float worst_f32(u64 wd) {
+    return __double2float_ru(__longlong_as_double((long long)wd));
+}
+
+// One chunk of candidates (one per lane, `valid` lanes only): reject by the
+// FP32 lower bound, compute exact keys for the rest, insert the ones that beat
+// the current worst.  x32/c32: FP32 coordinates; pexact: FP64 coordinates of
+// the candidate (read only if it passes).
+template <int DIM>
+__device__ __forceinline__ void consider(TopList &tl, bool valid, const float *x32, const float *c32,
+                                         const double *pexact, const double *c, int idx,
+                                         float delta, u64 &wd, int &wi, bool &dup) {
+    bool pass = false;
+    if (valid) {
+        float d2f = 0.0f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const float t = x32[a] - c32[a];
+            d2f = fmaf(t, t, d2f);
+        }
+        const float lo = fmaxf(sqrtf(d2f) - delta, 0.0f);
+        pass = lo * lo <= worst_f32(wd) * 1.000001f;
+    }
+    u64 key = kInfBits;
+    if (__any_sync(kFull, pass) && pass) {
+        const double d2 = dist2_rn<DIM>(pexact, c);
+        key = (u64)__double_as_longlong(d2);
+        if (d2 == 0.0) dup = true;
+    }
+    unsigned m = __ballot_sync(kFull, pass && key_lt(key, idx, wd, wi));
     while (m) {
-        int src = __ffs(m) - 1;
+        const int src = __ffs(m) - 1;
         m &= m - 1;
-        double cd = __shfl_sync(kFull, d, src);
-        int ci = __shfl_sync(kFull, idx, src);
-        if (key_lt(cd, ci, wd, wi)) {
-            tl.insert(cd, ci);
+        const u64 ck = __shfl_sync(kFull, key, src);
+        const int ci = __shfl_sync(kFull, idx, src);
+        if (key_lt(ck, ci, wd, wi)) {
+            tl.insert(ck, ci);
             tl.worst(wd, wi);
         }
     }
@@ -302,9 +370,9 @@ __device__ __forceinline__ void offer(TopList &tl, bool valid, double d, int idx
 
 __device__ __forceinline__ void write_row(const TopList &tl, int64_t q, int n, int32_t *out_row,
                                           int32_t *status, bool dup) {
-    int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     if (lane == 0) out_row[0] = (int32_t)q;
-    int K = n - 1;
+    const int K = n - 1;
     bool full = true;
     if (lane < K) {
         out_row[1 + lane] = tl.ilo == 0x7fffffff ? -1 : tl.ilo;
@@ -322,37 +390,41 @@ __device__ __forceinline__ void write_row(const TopList &tl, int64_t q, int n, i
 template <int DIM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__restrict__ start,
-           const double *__restrict__ spts, const int *__restrict__ sidx, int64_t q_begin,
-           int64_t q_end, int n, int32_t *__restrict__ out, int32_t *status) {
+           const double *__restrict__ spts, const float *__restrict__ spts32,
+           const int *__restrict__ sidx, int64_t q_begin, int64_t q_end, int n,
+           int32_t *__restrict__ out, int32_t *status) {
     const GridParams g = *gp;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double slack = 1e-9 * g.cell;
+    const float delta = g.delta32;
+    const float slack = 2.0f * delta + 1e-6f * g.cell32;
+    int maxdim = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) maxdim = max(maxdim, g.dims[a]);
     for (int64_t q = q_begin + warp0; q < q_end; q += nwarps) {
         double c[DIM];
+        float c32[DIM];
         int cq[DIM];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             c[a] = pts[q * DIM + a];
+            c32[a] = (float)c[a];
             cq[a] = cell_coord<DIM>(c[a], a, g);
         }
         TopList tl;
         tl.init(n - 1);
-        double wd;
+        u64 wd;
         int wi;
         tl.worst(wd, wi);
         bool dup = false;
-        int maxdim = 0;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) maxdim = max(maxdim, g.dims[a]);
         for (int t = 0; t <= maxdim; ++t) {
             const int side = 2 * t + 1;
             int ncube = side;
 #pragma unroll
             for (int a = 1; a < DIM; ++a) ncube *= side;
             for (int u0 = 0; u0 < ncube; u0 += 32) {
-                int u = u0 + lane;
+                const int u = u0 + lane;
                 int cstart = 0, ccount = 0;
                 if (u < ncube) {
                     int off[DIM], rem = u, cheb = 0;
@@ -364,66 +436,68 @@ k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__re
                         rem /= side;
                         cheb = max(cheb, abs(off[a]));
                     }
-                    double md2 = 0.0;
+                    float md2 = 0.0f;
 #pragma unroll
                     for (int a = DIM - 1; a >= 0; --a) {
-                        int ca = cq[a] + off[a];
+                        const int ca = cq[a] + off[a];
                         inside &= (ca >= 0 && ca < g.dims[a]);
                         cid = cid * g.dims[a] + ca;
-                        double blo = g.lo[a] + ca * g.cell - slack;
-                        double bhi = g.lo[a] + (ca + 1) * g.cell + slack;
-                        double gap = fmax(0.0, fmax(blo - c[a], c[a] - bhi));
-                        md2 += gap * gap;
+                        const float blo = fmaf((float)ca, g.cell32, g.lo32[a]) - slack;
+                        const float bhi = fmaf((float)(ca + 1), g.cell32, g.lo32[a]) + slack;
+                        const float gap = fmaxf(0.0f, fmaxf(blo - c32[a], c32[a] - bhi));
+                        md2 = fmaf(gap, gap, md2);
                     }
-                    if (inside && cheb == t && !(md2 * (1.0 - 1e-12) > wd)) {
+                    if (inside && cheb == t && !(md2 * 0.99999f > worst_f32(wd))) {
                         cstart = start[cid];
                         ccount = start[cid + 1] - cstart;
                     }
                 }
                 // inclusive scan of counts over the warp
                 int incl = ccount;
+#pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(kFull, incl, o);
+                    const int y = __shfl_up_sync(kFull, incl, o);
                     if (lane >= o) incl += y;
                 }
-                int total = __shfl_sync(kFull, incl, 31);
+                const int total = __shfl_sync(kFull, incl, 31);
                 for (int p0 = 0; p0 < total; p0 += 32) {
-                    int p = p0 + lane;
+                    const int p = p0 + lane;
                     int owner = 0;
 #pragma unroll
                     for (int step = 16; step; step >>= 1) {
-                        int probe = __shfl_sync(kFull, incl, owner + step - 1);
+                        const int probe = __shfl_sync(kFull, incl, owner + step - 1);
                         if (probe <= p) owner += step;
                     }
-                    int os = __shfl_sync(kFull, cstart, owner);
-                    int oi = __shfl_sync(kFull, incl, owner);
-                    int oc = __shfl_sync(kFull, ccount, owner);
+                    const int os = __shfl_sync(kFull, cstart, owner);
+                    const int oi = __shfl_sync(kFull, incl, owner);
+                    const int oc = __shfl_sync(kFull, ccount, owner);
                     bool valid = p < total;
-                    double d2 = 0.0;
-                    int idx = -1;
+                    int sp = 0, idx = -1;
+                    float x32[DIM];
                     if (valid) {
-                        int sp = os + (p - (oi - oc));
+                        sp = os + (p - (oi - oc));
                         idx = sidx[sp];
-                        d2 = dist2_rn<DIM>(spts + (int64_t)sp * DIM, c);
-                        if (idx == (int)q) valid = false;
-                        else if (d2 == 0.0) dup = true;
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a) x32[a] = spts32[(int64_t)sp * DIM + a];
+                        valid = idx != (int)q;
                     }
-                    offer(tl, valid, d2, idx, wd, wi);
+                    consider<DIM>(tl, valid, x32, c32, spts + (int64_t)sp * DIM, c, idx, delta, wd,
+                                  wi, dup);
                 }
             }
             // stop once every unvisited cell is provably farther than the worst kept
             bool covers = true;
-            double bd = DBL_MAX;
+            float bd = 3.0e38f;
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
-                bool lo_edge = cq[a] - t <= 0, hi_edge = cq[a] + t >= g.dims[a] - 1;
+                const bool lo_edge = cq[a] - t <= 0, hi_edge = cq[a] + t >= g.dims[a] - 1;
                 covers &= lo_edge && hi_edge;
-                if (!lo_edge) bd = fmin(bd, c[a] - (g.lo[a] + (cq[a] - t) * g.cell) - slack);
-                if (!hi_edge) bd = fmin(bd, g.lo[a] + (cq[a] + t + 1) * g.cell + slack - c[a]);
+                if (!lo_edge) bd = fminf(bd, c32[a] - fmaf((float)(cq[a] - t), g.cell32, g.lo32[a]));
+                if (!hi_edge) bd = fminf(bd, fmaf((float)(cq[a] + t + 1), g.cell32, g.lo32[a]) - c32[a]);
             }
             if (covers) break;
-            bd = fmax(bd, 0.0);
-            if (bd * bd * (1.0 - 1e-12) > wd) break;
+            bd = fmaxf(bd - slack, 0.0f);
+            if (bd * bd * 0.99999f > worst_f32(wd)) break;
         }
         dup = __any_sync(kFull, dup);
         write_row(tl, q, n, out + (q - q_begin) * n, status, dup);
@@ -433,30 +507,35 @@ k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__re
 // ----------------------------------------------------------------- brute force
 template <int DIM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_knn_brute(const double *__restrict__ pts, int64_t N, int64_t q_begin, int64_t q_end, int n,
-            int32_t *__restrict__ out, int32_t *status) {
+k_knn_brute(const double *__restrict__ pts, const float *__restrict__ pts32, const float *dptr,
+            int64_t N, int64_t q_begin, int64_t q_end, int n, int32_t *__restrict__ out,
+            int32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float delta = *dptr;
     for (int64_t q = q_begin + warp0; q < q_end; q += nwarps) {
         double c[DIM];
+        float c32[DIM];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) c[a] = pts[q * DIM + a];
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = pts[q * DIM + a];
+            c32[a] = (float)c[a];
+        }
         TopList tl;
         tl.init(n - 1);
-        double wd;
+        u64 wd;
         int wi;
         tl.worst(wd, wi);
         bool dup = false;
         for (int64_t j0 = 0; j0 < N; j0 += 32) {
-            int64_t j = j0 + lane;
-            bool valid = j < N && j != q;
-            double d2 = 0.0;
-            if (valid) {
-                d2 = dist2_rn<DIM>(pts + j * DIM, c);
-                if (d2 == 0.0) dup = true;
-            }
-            offer(tl, valid, d2, (int)j, wd, wi);
+            const int64_t j = j0 + lane;
+            const bool valid = j < N && j != q;
+            const int64_t jj = j < N ? j : 0;
+            float x32[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) x32[a] = pts32[jj * DIM + a];
+            consider<DIM>(tl, valid, x32, c32, pts + jj * DIM, c, (int)j, delta, wd, wi, dup);
         }
         dup = __any_sync(kFull, dup);
         write_row(tl, q, n, out + (q - q_begin) * n, status, dup);
@@ -471,33 +550,48 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     cudaStream_t st = ctx->stream;
     const int qblocks = ctx->num_sms * 16;
     if (method == MM_KNN_AUTO) method = N <= 4096 ? MM_KNN_BRUTE : MM_KNN_GRID;
+    const int bb_blocks = std::min(ctx->num_sms * 2, (int)((N + 255) / 256) + 1);
+    const int eb = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 8);
     if (method == MM_KNN_BRUTE) {
+        WsCarve wc;
+        const size_t o_part = wc.take<double>((size_t)bb_blocks * 2 * DIM);
+        const size_t o_delta = wc.take<float>(1);
+        const size_t o_p32 = wc.take<float>((size_t)N * DIM);
+        char *ws = mm_workspace(ctx, wc.off);
+        if (!ws) return mm_fail(ctx, MM_ENOMEM, "knn workspace of %zu bytes", wc.off);
+        double *part = (double *)(ws + o_part);
+        float *delta = (float *)(ws + o_delta);
+        float *p32 = (float *)(ws + o_p32);
+        k_bbox_partial<DIM><<<bb_blocks, 256, 0, st>>>(d_pts, N, part);
+        k_brute_delta<DIM><<<1, 32, 0, st>>>(part, bb_blocks, delta);
+        k_to_fp32<DIM><<<eb, 256, 0, st>>>(d_pts, N, p32);
+        MM_LAUNCH_CHECK(ctx);
         for (int r = 0; r < nranges; ++r) {
             const mm_knn_range &R = ranges[r];
             if (R.q_end <= R.q_begin) continue;
-            int64_t warps = R.q_end - R.q_begin;
-            int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
-            k_knn_brute<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, N, R.q_begin, R.q_end,
-                                                                     R.n, R.d_idx, d_status);
+            const int64_t warps = R.q_end - R.q_begin;
+            const int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
+            k_knn_brute<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, p32, delta, N, R.q_begin,
+                                                                     R.q_end, R.n, R.d_idx, d_status);
             MM_LAUNCH_CHECK(ctx);
         }
         return MM_OK;
     }
     // ---- grid build
-    double ppc = fmax(2.0, nmax / double(1 << DIM));
-    int64_t cap = (int64_t)(4.0 * N / ppc) + 64;
-    const int bb_blocks = min(ctx->num_sms * 2, (int)((N + 255) / 256) + 1);
-    int ntiles = (int)((cap + kScanTile - 1) / kScanTile);
+    const double ppc = fmax(2.0, nmax / double(1 << DIM));
+    const int64_t cap = (int64_t)(4.0 * N / ppc) + 64;
+    const int ntiles = (int)((cap + kScanTile - 1) / kScanTile);
     WsCarve wc;
-    size_t o_part = wc.take<double>((size_t)bb_blocks * 2 * DIM);
-    size_t o_gp = wc.take<GridParams>(1);
-    size_t o_count = wc.take<int>((size_t)cap + 1);
-    size_t o_start = wc.take<int>((size_t)cap + 1);
-    size_t o_cellof = wc.take<int>((size_t)N);
-    size_t o_rank = wc.take<int>((size_t)N);
-    size_t o_spts = wc.take<double>((size_t)N * DIM);
-    size_t o_sidx = wc.take<int>((size_t)N);
-    size_t o_tiles = wc.take<int>((size_t)ntiles + 1);
+    const size_t o_part = wc.take<double>((size_t)bb_blocks * 2 * DIM);
+    const size_t o_gp = wc.take<GridParams>(1);
+    const size_t o_count = wc.take<int>((size_t)cap + 1);
+    const size_t o_start = wc.take<int>((size_t)cap + 1);
+    const size_t o_cellof = wc.take<int>((size_t)N);
+    const size_t o_rank = wc.take<int>((size_t)N);
+    const size_t o_spts = wc.take<double>((size_t)N * DIM);
+    const size_t o_spts32 = wc.take<float>((size_t)N * DIM);
+    const size_t o_sidx = wc.take<int>((size_t)N);
+    const size_t o_tiles = wc.take<int>((size_t)ntiles + 1);
     char *ws = mm_workspace(ctx, wc.off);
     if (!ws) return mm_fail(ctx, MM_ENOMEM, "knn workspace of %zu bytes", wc.off);
     double *part = (double *)(ws + o_part);
@@ -505,8 +599,8 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     int *count = (int *)(ws + o_count), *start = (int *)(ws + o_start);
     int *cellof = (int *)(ws + o_cellof), *rank = (int *)(ws + o_rank);
     double *spts = (double *)(ws + o_spts);
+    float *spts32 = (float *)(ws + o_spts32);
     int *sidx = (int *)(ws + o_sidx), *tiles = (int *)(ws + o_tiles);
-    const int eb = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 8);
     k_bbox_partial<DIM><<<bb_blocks, 256, 0, st>>>(d_pts, N, part);
     k_grid_params<DIM><<<1, 32, 0, st>>>(part, bb_blocks, N, ppc, cap, gp);
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(cap + 1), st));
@@ -514,14 +608,14 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count, gp, start, tiles);
     k_scan_sums<<<1, kScanThreads, 0, st>>>(tiles, ntiles, gp, start);
     k_scan_add<<<ntiles, kScanThreads, 0, st>>>(tiles, gp, start);
-    k_scatter<DIM><<<eb, 256, 0, st>>>(d_pts, N, cellof, rank, start, spts, sidx);
+    k_scatter<DIM><<<eb, 256, 0, st>>>(d_pts, N, cellof, rank, start, spts, spts32, sidx);
     MM_LAUNCH_CHECK(ctx);
     for (int r = 0; r < nranges; ++r) {
         const mm_knn_range &R = ranges[r];
         if (R.q_end <= R.q_begin) continue;
-        int64_t warps = R.q_end - R.q_begin;
-        int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
-        k_knn_grid<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, gp, start, spts, sidx,
+        const int64_t warps = R.q_end - R.q_begin;
+        const int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
+        k_knn_grid<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, gp, start, spts, spts32, sidx,
                                                                 R.q_begin, R.q_end, R.n, R.d_idx,
                                                                 d_status);
         MM_LAUNCH_CHECK(ctx);
