@@ -163,6 +163,72 @@ int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N
                      const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
                      int n_max, int precision, double *const *d_vals, int32_t *d_status);
 
+/* ----------------------------------------------- batched (mixed) classes */
+/*
+ * One stencil class for mm_rbffd_weights_batched: the arguments of one
+ * mm_rbffd_weights call.  Classes may differ in dimension, node set, stencil
+ * size, degree, PHS exponent and operators.
+ */
+typedef struct {
+    unsigned ops;                 /* MM_LAP | MM_DX | ...                            */
+    int k, m, dim;
+    int64_t N;                    /* nodes of d_pts                                  */
+    const double *d_pts;          /* [N x dim]                                       */
+    const double *d_normals;      /* [N x dim] or NULL without MM_DN                 */
+    mm_csr_pattern stencils;      /* device CSR pattern (by value)                   */
+    int64_t row_begin, row_end;   /* rows of this class                              */
+    int n_max;                    /* largest stencil size in the rows                */
+    double *d_vals[5];            /* one array per set bit of ops, in bit order      */
+    int32_t *d_status;            /* [stencils.nrows] or NULL                        */
+} mm_weights_class;
+
+/* Launch shape of the persistent batched kernel. */
+typedef struct {
+    int warps_per_block;   /* stencils in flight per CTA (1..8)                      */
+    int blocks_per_sm;     /* resident CTAs per SM; grid = blocks_per_sm * SM count  */
+    int chunk_rows;        /* rows per work item taken from the queue                */
+} mm_launch_config;
+
+/*
+ * Weights of several stencil classes in ONE persistent launch (plus one
+ * FP64 launch for stencils the FP32 solver hands over).  The paper computes
+ * the weights of all nodes in one OpenMP loop (Section 5); here every warp
+ * repeatedly takes a chunk of rows of some class from an atomic work queue,
+ * so classes of very different cost share the GPU without a tail per class.
+ * Per class the results equal those of mm_rbffd_weights with the same
+ * arguments and precision (bit for bit; classes with 2 or 3 operators run on
+ * the 4-column solver whose spare column has a zero right-hand side).
+ *   nclasses   1..96 classes per call.
+ *   precision  MM_FP64 or MM_FP32_IR.  With MM_FP32_IR, classes with all
+ *              five operators are processed by separate launches in this call.
+ *   config     launch shape, or NULL: the context's tuned shape for this batch
+ *              signature (mm_autotune_batched), else a default.
+ * Graph capture: the call enqueues only kernels and memsets; class
+ * descriptors travel as a kernel parameter.  Make one call with the same
+ * classes before capturing it, so the context workspace is already large
+ * enough (growing it would allocate).
+ * Errors: as mm_rbffd_weights; MM_EBADARG for nclasses out of range.
+ */
+int mm_rbffd_weights_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *classes,
+                             int precision, const mm_launch_config *config);
+
+/*
+ * Autotuner for mm_rbffd_weights_batched: times candidate launch shapes
+ * (warps per CTA, CTAs per SM, rows per work item) on the first
+ * `sample_rows` rows of every class (0 = 16384) and stores the fastest in the
+ * context under the batch signature (dims, stencil sizes, degrees, operator
+ * counts, precision); later calls with config == NULL use it.  Writes weights
+ * of the sampled rows as a side effect.  Synchronises; not for use inside a
+ * stream capture.  *best and *best_ms (either may be NULL) receive the winner.
+ */
+int mm_autotune_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int precision,
+                        int64_t sample_rows, mm_launch_config *best, double *best_ms);
+
+/* Save / load the context's tuned launch shapes as a text table (one line per
+ * batch signature).  Loading merges into the context's table. */
+int mm_tile_table_save(const mm_ctx *ctx, const char *path);
+int mm_tile_table_load(mm_ctx *ctx, const char *path);
+
 /*
  * Allocation-free variant of mm_rbffd_weights with precision MM_FP32_IR.
  * The paper has no counterpart: this exists for callers that cannot allocate

@@ -24,7 +24,9 @@ OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX = 1, 2, 3
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
-           "mm_diffuse", "mm_measure_fma_peak", "mm_rbffd_weights_ir_noalloc"]
+           "mm_diffuse", "mm_measure_fma_peak", "mm_rbffd_weights_ir_noalloc",
+           "mm_rbffd_weights_batched", "mm_autotune_batched", "mm_tile_table_save",
+           "mm_tile_table_load"]
 
 
 class KnnRange(C.Structure):
@@ -35,6 +37,17 @@ class KnnRange(C.Structure):
 class CsrPattern(C.Structure):
     _fields_ = [("nrows", C.c_int64), ("nnz", C.c_int64), ("d_row_ptr", C.c_void_p),
                 ("d_col", C.c_void_p)]
+
+
+class WeightsClass(C.Structure):
+    _fields_ = [("ops", C.c_uint), ("k", C.c_int), ("m", C.c_int), ("dim", C.c_int),
+                ("N", C.c_int64), ("d_pts", C.c_void_p), ("d_normals", C.c_void_p),
+                ("stencils", CsrPattern), ("row_begin", C.c_int64), ("row_end", C.c_int64),
+                ("n_max", C.c_int), ("d_vals", C.c_void_p * 5), ("d_status", C.c_void_p)]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("chunk_rows", C.c_int)]
 
 
 class MMError(RuntimeError):
@@ -75,6 +88,12 @@ def load():
         lib.mm_rbffd_weights_ir_noalloc.argtypes = [vp, C.c_uint, C.c_int, C.c_int, C.c_int, i64,
                                                     vp, vp, C.POINTER(CsrPattern), i64, i64,
                                                     C.c_int, C.POINTER(vp), vp]
+        lib.mm_rbffd_weights_batched.argtypes = [vp, C.c_int, C.POINTER(WeightsClass), C.c_int,
+                                                 C.POINTER(LaunchConfig)]
+        lib.mm_autotune_batched.argtypes = [vp, C.c_int, C.POINTER(WeightsClass), C.c_int, i64,
+                                            C.POINTER(LaunchConfig), C.POINTER(dbl)]
+        lib.mm_tile_table_save.argtypes = [vp, C.c_char_p]
+        lib.mm_tile_table_load.argtypes = [vp, C.c_char_p]
         lib.mm_apply_operator.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, dbl, vp]
         lib.mm_diffuse.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, C.c_int, vp, vp]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
@@ -205,6 +224,57 @@ class Context:
         self._check(self._lib.mm_rbffd_weights_ir_noalloc(
             self._h, ops, k, m, dim, N, _ptr(pts), _ptr(normals), C.byref(pat), row_begin,
             row_end, n_max, vp, _ptr(status)))
+
+    @staticmethod
+    def weights_class(ops, k, m, pts, row_ptr, col, vals, row_begin=0, row_end=None, n_max=None,
+                      normals=None, status=None):
+        """Describe one stencil class for rbffd_weights_batched (tensors must
+        stay alive until the call has run)."""
+        _dev(pts, "pts", torch.float64)
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        N, dim = pts.shape
+        nrows = row_ptr.numel() - 1
+        nbits = bin(ops).count("1")
+        if len(vals) != nbits:
+            raise MMError(f"{nbits} value arrays expected")
+        if n_max is None:
+            raise MMError("n_max is required")
+        wc = WeightsClass()
+        wc.ops, wc.k, wc.m, wc.dim, wc.N = ops, k, m, dim, N
+        wc.d_pts = pts.data_ptr()
+        wc.d_normals = normals.data_ptr() if normals is not None else None
+        wc.stencils = CsrPattern(nrows, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        wc.row_begin = row_begin
+        wc.row_end = nrows if row_end is None else row_end
+        wc.n_max = n_max
+        for i, v in enumerate(vals):
+            _dev(v, "vals", torch.float64)
+            wc.d_vals[i] = v.data_ptr()
+        wc.d_status = status.data_ptr() if status is not None else None
+        return wc
+
+    def rbffd_weights_batched(self, classes, precision=FP64, config=None):
+        """mm_rbffd_weights_batched: all classes in one persistent launch.
+        config: (warps_per_block, blocks_per_sm, chunk_rows) or None."""
+        arr = (WeightsClass * len(classes))(*classes)
+        cfg = None if config is None else C.byref(LaunchConfig(*config))
+        self._check(self._lib.mm_rbffd_weights_batched(self._h, len(classes), arr, precision, cfg))
+
+    def autotune_batched(self, classes, precision=FP64, sample_rows=0):
+        """mm_autotune_batched; returns ((warps_per_block, blocks_per_sm, chunk_rows), ms)."""
+        arr = (WeightsClass * len(classes))(*classes)
+        best = LaunchConfig()
+        ms = C.c_double()
+        self._check(self._lib.mm_autotune_batched(self._h, len(classes), arr, precision,
+                                                  int(sample_rows), C.byref(best), C.byref(ms)))
+        return (best.warps_per_block, best.blocks_per_sm, best.chunk_rows), ms.value
+
+    def tile_table_save(self, path):
+        self._check(self._lib.mm_tile_table_save(self._h, str(path).encode()))
+
+    def tile_table_load(self, path):
+        self._check(self._lib.mm_tile_table_load(self._h, str(path).encode()))
 
     # ------------------------------------------------- operator application
     def apply_operator(self, row_ptr, col, vals, u, y, alpha=1.0, beta=0.0):

@@ -3,11 +3,14 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "mm_internal.cuh"
 
 int rbffd_init_device(mm_ctx *ctx);
+int batched_init_device(mm_ctx *ctx);
 
 int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...) {
     if (ctx) {
@@ -37,6 +40,18 @@ char *mm_workspace(mm_ctx *ctx, size_t bytes) {
     }
     ctx->ws_bytes = want;
     return ctx->ws;
+}
+
+cudaError_t mm_set_smem(const mm_ctx *ctx, const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> done;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(ctx->device, kernel);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done[key] = bytes;
+    return e;
 }
 
 namespace {
@@ -113,7 +128,7 @@ int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream) {
     }
     ctx->num_sms = sms;
     ctx->smem_optin = (size_t)optin;
-    if (rbffd_init_device(ctx) != MM_OK) {
+    if (rbffd_init_device(ctx) != MM_OK || batched_init_device(ctx) != MM_OK) {
         delete ctx;
         return MM_ECUDA;
     }

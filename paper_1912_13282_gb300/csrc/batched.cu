@@ -1,0 +1,415 @@
+// Persistent batched weights: all stencil classes of a call in one launch.
+//
+// The class descriptors travel by value in a __grid_constant__ kernel
+// parameter (no host memory is read when a captured graph replays).  Work
+// items are chunks of consecutive rows of one class; warps take them from an
+// atomic counter until the counter passes the total, so the loop is bounded
+// by the number of items.  The FP32 + FP64-refinement variant hands rows it
+// cannot finish to a second launch, the FP64 solver, through a queue of
+// (class, row) pairs.
+//
+// The autotuner times launch shapes on a sample of each class and keeps the
+// fastest per batch signature in the context (saved/loaded as a text table).
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "rbffd_dev.cuh"
+
+namespace {
+
+constexpr int kMaxBatchClasses = 96;
+typedef unsigned long long u64;
+
+struct BatchParams {
+    WParams cls[kMaxBatchClasses];
+    int64_t prefix[kMaxBatchClasses + 1];   // first work item of each class
+    signed char variant[kMaxBatchClasses];  // mixed-kernel shape per class
+    int nclasses;
+    int chunk_rows;
+    int64_t total_items;
+    int *queue;                             // work counter
+    u64 *fb_list;                           // (class << 32) | row
+    int *fb_count;
+    size_t warp_bytes;
+};
+
+static_assert(sizeof(BatchParams) <= 32000, "batched kernel parameters exceed the 32 KB limit");
+
+// Variant of a class for the mixed kernel: (dim, rows per lane, column count).
+// Classes with 2..4 operators run on the 4-column solver (the unused columns
+// carry a zero right-hand side and are not stored).
+__host__ __device__ inline int mixed_cols(int R) { return R == 1 ? 1 : 4; }
+__host__ __device__ inline int mixed_variant(int dim, int rpl, int R) {
+    const int rsel = R == 1 ? 0 : 1;
+    return ((dim - 2) * 3 + (rpl - 1)) * 2 + rsel;
+}
+
+template <int DIM, int RPL>
+__device__ bool mixed_dispatch_r(int rsel, const WParams &P, int64_t row, char *base) {
+    if (rsel == 0) return mixed_row<DIM, RPL, 1>(P, row, base);
+    return mixed_row<DIM, RPL, 4>(P, row, base);
+}
+
+template <int DIM>
+__device__ bool mixed_dispatch_d(int v, const WParams &P, int64_t row, char *base) {
+    const int rsel = v % 2, rpl = (v / 2) % 3 + 1;
+    if (rpl == 1) return mixed_dispatch_r<DIM, 1>(rsel, P, row, base);
+    if (rpl == 2) return mixed_dispatch_r<DIM, 2>(rsel, P, row, base);
+    return mixed_dispatch_r<DIM, 3>(rsel, P, row, base);
+}
+
+__device__ int class_of(const BatchParams &B, int64_t item) {
+    int lo = 0, hi = B.nclasses - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.prefix[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_weights_batched(const __grid_constant__ BatchParams B) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    char *base = (char *)smem + (size_t)wib * B.warp_bytes;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(B.queue, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= B.total_items) break;          // every item is taken once
+        const int c = class_of(B, item);
+        const WParams &P = B.cls[c];
+        const int64_t r0 = P.row_begin + (item - B.prefix[c]) * (int64_t)B.chunk_rows;
+        const int64_t r1 = min(r0 + (int64_t)B.chunk_rows, P.row_end);
+        const int v = B.variant[c];
+        for (int64_t row = r0; row < r1; ++row) {
+            if (MIXED) {
+                const bool q = P.dim == 2 ? mixed_dispatch_d<2>(v, P, row, base)
+                                          : mixed_dispatch_d<3>(v, P, row, base);
+                if (q && lane == 0) {
+                    const int slot = atomicAdd(B.fb_count, 1);
+                    B.fb_list[slot] = ((u64)c << 32) | (u64)row;
+                }
+                __syncwarp();
+            } else {
+                if (P.dim == 2) fp64_row<2>(P, row, (double *)base, false);
+                else fp64_row<3>(P, row, (double *)base, false);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_weights_batched_fallback(const __grid_constant__ BatchParams B) {
+    extern __shared__ double smem[];
+    const int wib = threadIdx.x >> 5;
+    double *base = (double *)((char *)smem + (size_t)wib * B.warp_bytes);
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t count = *B.fb_count;
+    for (int64_t t = gw; t < count; t += nw) {
+        const u64 e = B.fb_list[t];
+        const int c = (int)(e >> 32);
+        const int64_t row = (int64_t)(e & 0xffffffffULL);
+        const WParams &P = B.cls[c];
+        if (P.dim == 2) fp64_row<2>(P, row, base, true);
+        else fp64_row<3>(P, row, base, true);
+    }
+}
+
+// ------------------------------------------------------------------ host
+struct Prepared {
+    BatchParams *B = nullptr;        // host copy (large: heap)
+    std::vector<int> separate;       // classes launched on their own
+    int64_t rows = 0;
+    bool mixed = false;
+    std::string signature;
+};
+
+std::string signature_of(const std::vector<WParams> &cls, int precision) {
+    std::string s = precision == MM_FP64 ? "fp64" : "fp32ir";
+    char buf[96];
+    for (const WParams &P : cls) {
+        snprintf(buf, sizeof buf, ";d%d n%d m%d k%d R%d", P.dim, P.n_max, P.m, P.k, P.R);
+        s += buf;
+    }
+    return s;
+}
+
+mm_launch_config default_config(mm_ctx *ctx, size_t warp_bytes) {
+    mm_launch_config c;
+    c.warps_per_block = 4;
+    while (c.warps_per_block > 1 && warp_bytes * c.warps_per_block > 96 * 1024) c.warps_per_block /= 2;
+    c.blocks_per_sm = 0;   // filled from the occupancy calculator
+    c.chunk_rows = 16;
+    (void)ctx;
+    return c;
+}
+
+// Builds the kernel parameter block; classes the persistent kernel cannot
+// take (mixed precision with 5 operators) are listed in `separate`.
+int prepare(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int precision,
+            int64_t row_cap, Prepared &out, std::vector<WeightsJob> &jobs) {
+    out.mixed = precision == MM_FP32_IR;
+    std::vector<WParams> cls;
+    jobs.clear();
+    for (int i = 0; i < nclasses; ++i) {
+        const mm_weights_class &C = classes[i];
+        WeightsJob job{};
+        int rc = weights_job_from_args(ctx, C.ops, C.k, C.m, C.dim, C.N, C.d_pts, C.d_normals,
+                                       &C.stencils, C.row_begin, C.row_end, C.n_max, C.d_vals,
+                                       C.d_status, &job);
+        if (rc != MM_OK) return mm_fail(ctx, rc, "class %d: %s", i, ctx->err.c_str());
+        if (row_cap > 0 && job.row_end - job.row_begin > row_cap) job.row_end = job.row_begin + row_cap;
+        jobs.push_back(job);
+        WParams P = wparams_from_job(ctx, job);
+        if (out.mixed && P.R > 4) {
+            out.separate.push_back(i);
+            continue;
+        }
+        cls.push_back(P);
+    }
+    out.signature = signature_of(cls, precision);
+    BatchParams *B = new BatchParams();
+    memset(B, 0, sizeof(BatchParams));
+    B->nclasses = (int)cls.size();
+    size_t wb = 0;
+    for (size_t i = 0; i < cls.size(); ++i) {
+        B->cls[i] = cls[i];
+        const WParams &P = cls[i];
+        wb = std::max(wb, fp64_warp_doubles(P.M_max, P.pitch64, P.n_max, P.dim) * sizeof(double));
+        if (out.mixed) {
+            const int rpl = (P.M_max + 31) / 32;
+            wb = std::max(wb, mixed_layout(P.n_max, P.l, mixed_cols(P.R), P.dim).bytes);
+            B->variant[i] = (signed char)mixed_variant(P.dim, rpl, P.R);
+        }
+        out.rows += P.row_end - P.row_begin;
+    }
+    B->warp_bytes = (wb + 15) & ~size_t(15);
+    out.B = B;
+    return MM_OK;
+}
+
+// Occupancy query, cached per (device, kernel, block, shared memory) so a
+// warmed-up call makes no such query inside a stream capture.
+cudaError_t occupancy(const mm_ctx *ctx, const void *kern, int threads, size_t sm, int *out) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(ctx->device, kern, threads, sm);
+    auto it = cache.find(key);
+    if (it != cache.end()) { *out = it->second; return cudaSuccess; }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, threads, sm);
+    if (e == cudaSuccess) cache[key] = *out;
+    return e;
+}
+
+int launch_prepared(mm_ctx *ctx, Prepared &pr, const mm_launch_config &cfg_in) {
+    BatchParams &B = *pr.B;
+    if (B.nclasses == 0) return MM_OK;
+    mm_launch_config cfg = cfg_in;
+    if (cfg.warps_per_block < 1 || cfg.warps_per_block > 8 || cfg.chunk_rows < 1)
+        return mm_fail(ctx, MM_EBADARG, "bad launch config");
+    const size_t sm = B.warp_bytes * cfg.warps_per_block;
+    if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: %zu bytes of shared memory per CTA", sm);
+    B.chunk_rows = cfg.chunk_rows;
+    int64_t items = 0;
+    for (int i = 0; i < B.nclasses; ++i) {
+        B.prefix[i] = items;
+        const int64_t rows = B.cls[i].row_end - B.cls[i].row_begin;
+        items += (rows + cfg.chunk_rows - 1) / cfg.chunk_rows;
+    }
+    B.prefix[B.nclasses] = items;
+    B.total_items = items;
+    if (items >= (int64_t(1) << 31)) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: too many work items");
+    WsCarve wc;
+    const size_t o_q = wc.take<int>(2);
+    const size_t o_fb = pr.mixed ? wc.take<u64>((size_t)pr.rows + 1) : 0;
+    char *ws = mm_workspace(ctx, wc.off);
+    if (!ws) return mm_fail(ctx, MM_ENOMEM, "batched workspace of %zu bytes", wc.off);
+    B.queue = (int *)(ws + o_q);
+    B.fb_count = B.queue + 1;
+    B.fb_list = pr.mixed ? (u64 *)(ws + o_fb) : nullptr;
+    cudaStream_t st = ctx->stream;
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(B.queue, 0, 2 * sizeof(int), st));
+    const void *kern = pr.mixed ? (const void *)k_weights_batched<true> : (const void *)k_weights_batched<false>;
+    MM_CUDA_CHECK(ctx, mm_set_smem(ctx, kern, sm));
+    int per_sm = cfg.blocks_per_sm;
+    if (per_sm <= 0) {
+        int occ = 0;
+        MM_CUDA_CHECK(ctx, occupancy(ctx, kern, cfg.warps_per_block * 32, sm, &occ));
+        per_sm = std::max(occ, 1);
+    }
+    const int blocks = per_sm * ctx->num_sms;
+    if (pr.mixed) k_weights_batched<true><<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
+    else k_weights_batched<false><<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
+    MM_LAUNCH_CHECK(ctx);
+    if (pr.mixed) {
+        MM_CUDA_CHECK(ctx, mm_set_smem(ctx, (const void *)k_weights_batched_fallback, sm));
+        const int fb_blocks = (int)std::min<int64_t>((pr.rows + cfg.warps_per_block - 1) / cfg.warps_per_block,
+                                                     (int64_t)ctx->num_sms * 8);
+        k_weights_batched_fallback<<<std::max(fb_blocks, 1), cfg.warps_per_block * 32, sm, st>>>(B);
+        MM_LAUNCH_CHECK(ctx);
+    }
+    return MM_OK;
+}
+
+int run_separate(mm_ctx *ctx, const Prepared &pr, const std::vector<WeightsJob> &jobs, int precision) {
+    for (int i : pr.separate) {
+        int rc = weights_launch(ctx, jobs[i], precision);
+        if (rc != MM_OK) return rc;
+    }
+    return MM_OK;
+}
+
+}  // namespace
+
+int batched_init_device(mm_ctx *ctx) {
+    MonoTable t;
+    mono_table_host(t);
+    MM_CUDA_CHECK(ctx, cudaMemcpyToSymbol(c_mono, &t, sizeof(t)));
+    return MM_OK;
+}
+
+extern "C" {
+
+int mm_rbffd_weights_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *classes,
+                             int precision, const mm_launch_config *config) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (nclasses < 1 || nclasses > kMaxBatchClasses || !classes)
+        return mm_fail(ctx, MM_EBADARG, "nclasses must be in [1, %d]", kMaxBatchClasses);
+    if (precision != MM_FP64 && precision != MM_FP32_IR)
+        return mm_fail(ctx, MM_EBADARG, "unknown precision %d", precision);
+    DeviceGuard g(ctx);
+    Prepared pr;
+    std::vector<WeightsJob> jobs;
+    int rc = prepare(ctx, nclasses, classes, precision, 0, pr, jobs);
+    if (rc == MM_OK) {
+        mm_launch_config cfg;
+        if (config) cfg = *config;
+        else {
+            auto it = ctx->tiles.find(pr.signature);
+            cfg = it != ctx->tiles.end() ? it->second : default_config(ctx, pr.B->warp_bytes);
+        }
+        rc = launch_prepared(ctx, pr, cfg);
+        if (rc == MM_OK) rc = run_separate(ctx, pr, jobs, precision);
+    }
+    delete pr.B;
+    return rc;
+}
+
+int mm_autotune_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int precision,
+                        int64_t sample_rows, mm_launch_config *best, double *best_ms) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (nclasses < 1 || nclasses > kMaxBatchClasses || !classes)
+        return mm_fail(ctx, MM_EBADARG, "nclasses must be in [1, %d]", kMaxBatchClasses);
+    if (precision != MM_FP64 && precision != MM_FP32_IR)
+        return mm_fail(ctx, MM_EBADARG, "unknown precision %d", precision);
+    if (sample_rows <= 0) sample_rows = 16384;
+    DeviceGuard g(ctx);
+    Prepared pr;
+    std::vector<WeightsJob> jobs;
+    int rc = prepare(ctx, nclasses, classes, precision, sample_rows, pr, jobs);
+    if (rc != MM_OK) { delete pr.B; return rc; }
+    // full-size signature: the sample only truncates row ranges
+    mm_launch_config best_cfg = default_config(ctx, pr.B->warp_bytes);
+    double best_t = 1e300;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int wpbs[] = {1, 2, 4, 8};
+    const int chunks[] = {4, 16, 64};
+    for (int wpb : wpbs) {
+        const size_t sm = pr.B->warp_bytes * wpb;
+        if (sm > ctx->smem_optin) continue;
+        const void *kern = pr.mixed ? (const void *)k_weights_batched<true> : (const void *)k_weights_batched<false>;
+        if (mm_set_smem(ctx, kern, sm) != cudaSuccess) { cudaGetLastError(); continue; }
+        int occ = 0;
+        if (occupancy(ctx, kern, wpb * 32, sm, &occ) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        for (int bps = std::max(1, occ / 2); bps <= occ; bps = bps == occ ? occ + 1 : std::min(occ, bps * 2)) {
+            for (int ch : chunks) {
+                mm_launch_config c{wpb, bps, ch};
+                rc = launch_prepared(ctx, pr, c);           // warm-up
+                if (rc != MM_OK) break;
+                float total = 0.f;
+                for (int rep = 0; rep < 3 && rc == MM_OK; ++rep) {
+                    cudaEventRecord(e0, ctx->stream);
+                    rc = launch_prepared(ctx, pr, c);
+                    cudaEventRecord(e1, ctx->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    total += ms;
+                }
+                if (rc != MM_OK) break;
+                if (total / 3 < best_t) { best_t = total / 3; best_cfg = c; }
+            }
+            if (rc != MM_OK) break;
+        }
+        if (rc != MM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    delete pr.B;
+    if (rc != MM_OK) return rc;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return mm_fail(ctx, MM_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    // key the table by the full-size signature (row counts do not enter it)
+    ctx->tiles[pr.signature] = best_cfg;
+    if (best) *best = best_cfg;
+    if (best_ms) *best_ms = best_t;
+    return MM_OK;
+}
+
+int mm_tile_table_save(const mm_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MM_EBADARG;
+    FILE *f = fopen(path, "w");
+    if (!f) return MM_EBADARG;
+    fprintf(f, "# libmm batched-weights launch shapes: signature|warps_per_block|blocks_per_sm|chunk_rows\n");
+    for (const auto &kv : ctx->tiles)
+        fprintf(f, "%s|%d|%d|%d\n", kv.first.c_str(), kv.second.warps_per_block, kv.second.blocks_per_sm,
+                kv.second.chunk_rows);
+    fclose(f);
+    return MM_OK;
+}
+
+int mm_tile_table_load(mm_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MM_EBADARG;
+    FILE *f = fopen(path, "r");
+    if (!f) return mm_fail(ctx, MM_EBADARG, "cannot open %s", path);
+    char line[4096];
+    int rc = MM_OK;
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        std::string s(line);
+        while (!s.empty() && (s.back() == '\n' || s.back() == '\r')) s.pop_back();
+        size_t p3 = s.rfind('|');
+        size_t p2 = p3 == std::string::npos ? p3 : s.rfind('|', p3 - 1);
+        size_t p1 = p2 == std::string::npos || p2 == 0 ? std::string::npos : s.rfind('|', p2 - 1);
+        if (p1 == std::string::npos) { rc = mm_fail(ctx, MM_EBADARG, "bad tile table line"); break; }
+        mm_launch_config c;
+        c.warps_per_block = atoi(s.substr(p1 + 1, p2 - p1 - 1).c_str());
+        c.blocks_per_sm = atoi(s.substr(p2 + 1, p3 - p2 - 1).c_str());
+        c.chunk_rows = atoi(s.substr(p3 + 1).c_str());
+        if (c.warps_per_block < 1 || c.warps_per_block > 8 || c.chunk_rows < 1 || c.blocks_per_sm < 0) {
+            rc = mm_fail(ctx, MM_EBADARG, "bad tile table entry");
+            break;
+        }
+        ctx->tiles[s.substr(0, p1)] = c;
+    }
+    fclose(f);
+    return rc;
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 
 #include "mm.h"
@@ -21,10 +22,17 @@ struct mm_ctx {
     double ir_tol = 1e-9;
     int ir_max_steps = 4;
     double kappa_max = 0.1;
+    // tuned launch shapes of the batched weights kernel, by batch signature
+    std::map<std::string, mm_launch_config> tiles;
 };
 
 // Records a message and returns `code`.
 int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...);
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when `bytes` exceeds
+// what was set before for this kernel on this device (so launches inside a
+// stream capture make no attribute call once warmed up).
+cudaError_t mm_set_smem(const mm_ctx *ctx, const void *kernel, size_t bytes);
 
 // Ensures the workspace holds at least `bytes`; returns its base or nullptr.
 char *mm_workspace(mm_ctx *ctx, size_t bytes);

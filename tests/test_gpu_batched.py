@@ -1,0 +1,195 @@
+"""Persistent batched weights (several stencil classes and node sets in one
+launch), CUDA-graph capture of batched weights + explicit diffusion, and the
+launch-shape autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import nodesets as NS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1912_13282_gb300 import _build
+    _build.build()
+    import paper_1912_13282_gb300 as pkg
+    return pkg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+class Geometry:
+    """A node set with kNN stencils per class and value arrays per operator."""
+
+    def __init__(self, P, ctx, ns, spec):
+        self.ns = ns
+        self.pts = dev(ns.pts)
+        self.nrm = dev(ns.normals)
+        sizes = np.zeros(ns.N, dtype=np.int64)
+        for cname, n, *_ in spec:
+            b, e = ns.classes[cname]
+            sizes[b:e] = n
+        rp = np.zeros(ns.N + 1, dtype=np.int64)
+        np.cumsum(sizes, out=rp[1:])
+        self.rp_h = rp
+        self.rp = dev(rp)
+        self.col = torch.empty(int(rp[-1]), dtype=torch.int32, device="cuda")
+        ranges = []
+        for cname, n, *_ in spec:
+            b, e = ns.classes[cname]
+            ranges.append((b, e, n, self.col[int(rp[b]):int(rp[e])]))
+        ctx.knn_stencils(self.pts, ranges, method=P.KNN_GRID)
+        self.spec = spec
+        self.status = torch.full((ns.N,), -1, dtype=torch.int32, device="cuda")
+
+    def new_vals(self):
+        names = sorted({nm for *_, ops in self.spec for nm in range(5) if ops & (1 << nm)})
+        return {b: torch.zeros(int(self.rp_h[-1]), dtype=torch.float64, device="cuda") for b in names}
+
+    def classes(self, P, vals):
+        out = []
+        for cname, n, k, m, ops in self.spec:
+            b, e = self.ns.classes[cname]
+            vv = [vals[bit] for bit in range(5) if ops & (1 << bit)]
+            out.append(P.Context.weights_class(ops, k, m, self.pts, self.rp, self.col, vv,
+                                               row_begin=b, row_end=e, n_max=n, normals=self.nrm,
+                                               status=self.status))
+        return out
+
+    def per_class(self, P, ctx, vals, precision):
+        for cname, n, k, m, ops in self.spec:
+            b, e = self.ns.classes[cname]
+            vv = [vals[bit] for bit in range(5) if ops & (1 << bit)]
+            ctx.rbffd_weights(ops, k, m, self.pts, self.rp, self.col, vv, row_begin=b, row_end=e,
+                              n_max=n, precision=precision, normals=self.nrm, status=self.status)
+
+
+def mixed_batch(P, ctx):
+    geoms = [
+        Geometry(P, ctx, NS.ball(20000, seed=31), [("interior", 35, 3, 2, 1 | 2 | 4 | 8),
+                                                   ("refined", 60, 3, 3, 1 | 2 | 4 | 8),
+                                                   ("boundary", 45, 3, 2, 16)]),
+        Geometry(P, ctx, NS.disk_holes(15000, seed=32), [("interior", 25, 5, 4, 1 | 2 | 4),
+                                                         ("boundary", 30, 5, 4, 16)]),
+        Geometry(P, ctx, NS.square(0.02, seed=33), [("interior", 12, 3, 2, 1 | 2 | 4),
+                                                    ("boundary", 12, 3, 2, 1)]),
+    ]
+    return geoms
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+def test_batched_equals_per_class(P, precision):
+    ctx = P.Context(0)
+    prec = P.FP64 if precision == "fp64" else P.FP32_IR
+    geoms = mixed_batch(P, ctx)
+    ref = []
+    for g in geoms:
+        v = g.new_vals()
+        g.per_class(P, ctx, v, prec)
+        torch.cuda.synchronize()
+        ref.append(({b: t.cpu().numpy() for b, t in v.items()}, g.status.cpu().numpy().copy()))
+    for cfg in (None, (1, 1, 4), (2, 0, 64)):
+        outs, classes = [], []
+        for g in geoms:
+            v = g.new_vals()
+            g.status.fill_(-1)
+            outs.append(v)
+            classes += g.classes(P, v)
+        ctx.rbffd_weights_batched(classes, precision=prec, config=cfg)
+        torch.cuda.synchronize()
+        for g, v, (rv, rs) in zip(geoms, outs, ref):
+            assert np.array_equal(g.status.cpu().numpy(), rs)
+            for b in v:
+                assert np.array_equal(v[b].cpu().numpy(), rv[b]), (cfg, b)
+        assert set(np.unique(np.concatenate([r[1] for r in ref]))) <= {0, P.binding.ST_FALLBACK}
+    ctx.close()
+
+
+def test_batched_weights_and_diffusion_in_one_graph(P):
+    """Batched FP32+refined weights of several 2D/3D node sets and 10 explicit
+    diffusion steps each, captured in one CUDA graph and replayed twice: the
+    replays reproduce the eager results."""
+    ctx = P.Context(0)
+    specs = [(NS.disk_holes(8000, seed=41), 12, 3, 2), (NS.disk_holes(12000, seed=42), 25, 5, 4),
+             (NS.ball(9000, seed=43), 35, 3, 2), (NS.ball(7000, seed=44), 60, 3, 3)]
+    geoms, fixed, u0s = [], [], []
+    for ns, n, k, m in specs:
+        # every node gets a Laplacian stencil; boundary rows are held fixed
+        ns.classes = {"all": (0, ns.N)}
+        g = Geometry(P, ctx, ns, [("all", n, k, m, 1)])
+        geoms.append(g)
+        b0 = ns.normals.any(axis=1)
+        fixed.append(dev(b0.astype(np.uint8)))
+        u0s.append(dev(NS.sin_product(ns.pts)))
+    vals = [g.new_vals() for g in geoms]
+    classes = sum((g.classes(P, v) for g, v in zip(geoms, vals)), [])
+    us = [u.clone() for u in u0s]
+    work = [torch.empty_like(u) for u in us]
+    dts = [0.05 * g.ns.h ** 2 for g in geoms]
+
+    def run():
+        ctx.rbffd_weights_batched(classes, precision=P.FP32_IR)
+        for g, v, f, u, w, dt in zip(geoms, vals, fixed, us, work, dts):
+            ctx.diffuse(g.rp, g.col, v[0], f, dt, 10, u, w)
+
+    run()                                   # eager (also sizes the workspace)
+    torch.cuda.synchronize()
+    eager_u = [u.cpu().numpy().copy() for u in us]
+    eager_w = [v[0].cpu().numpy().copy() for v in vals]
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for u, u0 in zip(us, u0s):
+            u.copy_(u0)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            ctx.set_stream(side)
+            run()
+    torch.cuda.synchronize()
+    ctx.set_stream(torch.cuda.current_stream())
+    for rep in range(2):
+        for u, u0, v in zip(us, u0s, vals):
+            u.copy_(u0)
+            v[0].zero_()
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        for u, e, v, ew in zip(us, eager_u, vals, eager_w):
+            assert np.array_equal(v[0].cpu().numpy(), ew)
+            assert np.array_equal(u.cpu().numpy(), e)
+    ctx.close()
+
+
+def test_autotune_and_tile_table(P, tmp_path):
+    ctx = P.Context(0)
+    geoms = mixed_batch(P, ctx)
+    vals = [g.new_vals() for g in geoms]
+    classes = sum((g.classes(P, v) for g, v in zip(geoms, vals)), [])
+    cfg, ms = ctx.autotune_batched(classes, precision=P.FP32_IR, sample_rows=2048)
+    assert 1 <= cfg[0] <= 8 and cfg[1] >= 1 and cfg[2] >= 1 and ms > 0
+    path = tmp_path / "tiles.txt"
+    ctx.tile_table_save(path)
+    text = path.read_text()
+    assert "fp32ir;d3 n35 m2 k3 R4;d3 n60 m3 k3 R4" in text
+    ctx2 = P.Context(0)
+    ctx2.tile_table_load(path)
+    ctx2.tile_table_save(tmp_path / "tiles2.txt")
+    assert (tmp_path / "tiles2.txt").read_text() == text
+    # tuned and default launch shapes give identical weights
+    ctx.rbffd_weights_batched(classes, precision=P.FP32_IR)           # tuned entry
+    torch.cuda.synchronize()
+    tuned = [{b: t.cpu().numpy() for b, t in v.items()} for v in vals]
+    ctx.rbffd_weights_batched(classes, precision=P.FP32_IR, config=(1, 0, 16))
+    torch.cuda.synchronize()
+    for v, t in zip(vals, tuned):
+        for b in v:
+            assert np.array_equal(v[b].cpu().numpy(), t[b])
+    ctx.close()
+    ctx2.close()
