@@ -278,6 +278,73 @@ int mm_apply_operator(mm_ctx *ctx, const mm_csr_pattern *stencils, const double 
 int mm_diffuse(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
                const uint8_t *d_fixed, double dt, int steps, double *d_u, double *d_work);
 
+/* ------------------------------------------------- learned surrogate (MLP) */
+/*
+ * A GELU multilayer perceptron n_in -> 256 -> 256 -> 256 -> n_out that maps
+ * the scaled offsets of a 2D stencil (features, see mm_stencil_features) to
+ * its scaled Laplacian weights.  No counterpart in the paper: it is trained
+ * on weights this library computes.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores, FP32 master parameters updated by Adam.
+ * Parameters in the plain layout W1 [256 x n_in], b1, W2 [256 x 256], b2,
+ * W3, b3, W4 [n_out x 256], b4 (row-major [out][in]) as FP32 host arrays.
+ * The network predicts (y - mean)/std per output (mm_mlp_set_output_scaling).
+ */
+typedef struct mm_mlp mm_mlp;
+
+/* Create with U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from `seed`, zero
+ * biases.  Supported: hidden == 256, n_layers == 3, n_in <= 64, n_out <= 32.
+ * The network owns its device buffers (params, Adam state, activations for
+ * 65536 rows).  Errors: MM_EUNSUPPORTED, MM_ENOMEM, MM_ECUDA. */
+int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers, int n_out,
+                  uint64_t seed);
+void mm_mlp_destroy(mm_mlp *net);
+int64_t mm_mlp_num_params(const mm_mlp *net);
+/* Host parameter arrays in the plain layout (mm_mlp_num_params floats); both synchronise. */
+int mm_mlp_set_params(mm_ctx *ctx, mm_mlp *net, const float *h_params);
+int mm_mlp_get_params(mm_ctx *ctx, const mm_mlp *net, float *h_params);
+/* Output scaling: targets are learned as (y - mean[c]) / std[c]; host arrays [n_out]. */
+int mm_mlp_set_output_scaling(mm_ctx *ctx, mm_mlp *net, const float *h_mean, const float *h_std);
+/* d_y [B x n_out] = network(d_x [B x n_in]) (FP32 in and out, scaling undone). */
+int mm_mlp_forward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, float *d_y);
+/* One Adam step (lr; beta 0.9/0.999, eps 1e-8) on the mean squared error over
+ * B <= 65536 rows of targets d_t [B x n_out]; d_loss (device, optional)
+ * receives the loss before the step. */
+int mm_mlp_train_step(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, const float *d_t,
+                      float lr, float *d_loss);
+/* Gradient of the same loss w.r.t. the parameters, plain layout, into host
+ * h_grads (no update); h_loss optional.  Synchronises. */
+int mm_mlp_grad(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, const float *d_t,
+                float *h_grads, float *h_loss);
+/* Checkpoint: FP32 parameters, Adam state, step count and output scaling. */
+int mm_mlp_save(mm_ctx *ctx, const mm_mlp *net, const char *path);
+int mm_mlp_load(mm_ctx *ctx, mm_mlp *net, const char *path);
+
+/*
+ * Features of stencils: for rows [row_begin, row_end) of n nodes each,
+ * d_x[(i - row_begin) * n * dim + j * dim + a] = (x_j - x_c)_a / s with
+ * s = max_j ||x_j - x_c|| (FP32), d_scale[i - row_begin] = s (optional).
+ * n <= 32.
+ */
+int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
+                        const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end, int n,
+                        float *d_x, double *d_scale);
+
+/*
+ * Laplacian weights through the surrogate: features -> network -> scaled
+ * weights w~; exact FP64 least-norm projection onto the monomial rows of
+ * eq. rbf-system-aug, (Q^T Q) z = l_q - Q^T w~, w = w~ + Q z (FP32 Cholesky of
+ * the Jacobi-scaled Gram matrix, FP64 constraint residuals until they hold to
+ * 1e-15 relative); judged by the other rows: rho = ||r - Q lambda||_inf /
+ * ||l_phi||_inf with r = l_phi - A w and lambda the least-squares multipliers
+ * (FP32).  rho <= tau: weights w / s^2 stored, status MM_ST_ACCEPTED;
+ * otherwise the FP64 solve (status MM_ST_FALLBACK).  2D only, n == n_out of
+ * the network, l <= 16.  d_rho (optional, [rows]) receives rho per row.
+ */
+int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, int64_t N,
+                               const double *d_pts, const mm_csr_pattern *stencils,
+                               int64_t row_begin, int64_t row_end, int n, double tau,
+                               double *d_lap_vals, int32_t *d_status, float *d_rho);
+
 /* ------------------------------------------------------------- measurement */
 /*
  * Measured arithmetic peak of this GPU for the pipe `which` (0 = FP64 FMA,

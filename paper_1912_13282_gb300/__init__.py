@@ -6,4 +6,4 @@ include/mm.h); ``binding`` is a thin ctypes layer over it.
 """
 from . import _build  # noqa: F401
 from .binding import (DN, DX, DY, DZ, FP32_IR, FP64, KNN_AUTO, KNN_BRUTE, KNN_GRID, LAP,  # noqa: F401
-                      Context, MMError, load)
+                      MLP, Context, MMError, load, rbffd_weights_surrogate, stencil_features)

@@ -26,7 +26,10 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
            "mm_diffuse", "mm_measure_fma_peak", "mm_rbffd_weights_ir_noalloc",
            "mm_rbffd_weights_batched", "mm_autotune_batched", "mm_tile_table_save",
-           "mm_tile_table_load"]
+           "mm_tile_table_load", "mm_mlp_create", "mm_mlp_destroy", "mm_mlp_num_params",
+           "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_output_scaling",
+           "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
+           "mm_stencil_features", "mm_rbffd_weights_surrogate"]
 
 
 class KnnRange(C.Structure):
@@ -94,12 +97,31 @@ def load():
                                             C.POINTER(LaunchConfig), C.POINTER(dbl)]
         lib.mm_tile_table_save.argtypes = [vp, C.c_char_p]
         lib.mm_tile_table_load.argtypes = [vp, C.c_char_p]
+        lib.mm_mlp_create.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]
+        lib.mm_mlp_destroy.argtypes = [vp]
+        lib.mm_mlp_destroy.restype = None
+        lib.mm_mlp_num_params.argtypes = [vp]
+        lib.mm_mlp_set_params.argtypes = [vp, vp, vp]
+        lib.mm_mlp_get_params.argtypes = [vp, vp, vp]
+        lib.mm_mlp_set_output_scaling.argtypes = [vp, vp, vp, vp]
+        lib.mm_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        lib.mm_mlp_train_step.argtypes = [vp, vp, i64, vp, vp, C.c_float, vp]
+        lib.mm_mlp_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+        lib.mm_mlp_save.argtypes = [vp, vp, C.c_char_p]
+        lib.mm_mlp_load.argtypes = [vp, vp, C.c_char_p]
+        lib.mm_stencil_features.argtypes = [vp, C.c_int, i64, vp, C.POINTER(CsrPattern), i64, i64,
+                                            C.c_int, vp, vp]
+        lib.mm_rbffd_weights_surrogate.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, i64, vp,
+                                                   C.POINTER(CsrPattern), i64, i64, C.c_int, dbl,
+                                                   vp, vp, vp]
         lib.mm_apply_operator.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, dbl, vp]
         lib.mm_diffuse.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, C.c_int, vp, vp]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
         for name in EXPORTS:
-            if name not in ("mm_ctx_destroy", "mm_last_error"):
+            if name not in ("mm_ctx_destroy", "mm_last_error", "mm_mlp_destroy",
+                            "mm_mlp_num_params"):
                 getattr(lib, name).restype = C.c_int
+        lib.mm_mlp_num_params.restype = i64
         _lib = lib
         return lib
 
@@ -302,3 +324,96 @@ class Context:
         out = C.c_double()
         self._check(self._lib.mm_measure_fma_peak(self._h, which, C.byref(out)))
         return out.value
+
+
+class MLP:
+    """The surrogate network (mm_mlp_*): 2D stencil features -> scaled
+    Laplacian weights."""
+
+    def __init__(self, ctx: Context, n_in: int, n_out: int, seed: int = 0):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        h = C.c_void_p()
+        ctx._check(self._lib.mm_mlp_create(ctx._h, C.byref(h), n_in, 256, 3, n_out, seed))
+        self._h = h
+        self.n_in, self.n_out = n_in, n_out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.mm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(self._lib.mm_mlp_num_params(self._h))
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        self.ctx._check(self._lib.mm_mlp_set_params(self.ctx._h, self._h, a.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.num_params, dtype=np.float32)
+        self.ctx._check(self._lib.mm_mlp_get_params(self.ctx._h, self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    def set_output_scaling(self, mean, std):
+        import numpy as np
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(std, dtype=np.float32)
+        self.ctx._check(self._lib.mm_mlp_set_output_scaling(self.ctx._h, self._h,
+                                                             m.ctypes.data_as(C.c_void_p),
+                                                             s.ctypes.data_as(C.c_void_p)))
+
+    def forward(self, x: torch.Tensor, y: torch.Tensor):
+        _dev(x, "x", torch.float32)
+        _dev(y, "y", torch.float32)
+        self.ctx._check(self._lib.mm_mlp_forward(self.ctx._h, self._h, x.shape[0], _ptr(x), _ptr(y)))
+
+    def train_step(self, x: torch.Tensor, t: torch.Tensor, lr: float, loss: torch.Tensor | None = None):
+        _dev(x, "x", torch.float32)
+        _dev(t, "t", torch.float32)
+        self.ctx._check(self._lib.mm_mlp_train_step(self.ctx._h, self._h, x.shape[0], _ptr(x), _ptr(t),
+                                                    float(lr), _ptr(loss)))
+
+    def grad(self, x: torch.Tensor, t: torch.Tensor):
+        import numpy as np
+        _dev(x, "x", torch.float32)
+        _dev(t, "t", torch.float32)
+        g = np.empty(self.num_params, dtype=np.float32)
+        loss = C.c_float()
+        self.ctx._check(self._lib.mm_mlp_grad(self.ctx._h, self._h, x.shape[0], _ptr(x), _ptr(t),
+                                              g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+        return float(loss.value), g
+
+    def save(self, path):
+        self.ctx._check(self._lib.mm_mlp_save(self.ctx._h, self._h, str(path).encode()))
+
+    def load(self, path):
+        self.ctx._check(self._lib.mm_mlp_load(self.ctx._h, self._h, str(path).encode()))
+
+
+def stencil_features(ctx: Context, pts, row_ptr, col, row_begin, row_end, n, x, scale=None):
+    _dev(pts, "pts", torch.float64)
+    pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+    ctx._check(ctx._lib.mm_stencil_features(ctx._h, pts.shape[1], pts.shape[0], _ptr(pts),
+                                            C.byref(pat), row_begin, row_end, n, _ptr(x),
+                                            _ptr(scale)))
+
+
+def rbffd_weights_surrogate(ctx: Context, net: MLP, k, m, pts, row_ptr, col, row_begin, row_end, n,
+                            tau, lap_vals, status=None, rho=None):
+    _dev(pts, "pts", torch.float64)
+    _dev(lap_vals, "lap_vals", torch.float64)
+    pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+    ctx._check(ctx._lib.mm_rbffd_weights_surrogate(ctx._h, net._h, k, m, pts.shape[1], pts.shape[0],
+                                                   _ptr(pts), C.byref(pat), row_begin, row_end, n,
+                                                   float(tau), _ptr(lap_vals), _ptr(status),
+                                                   _ptr(rho)))

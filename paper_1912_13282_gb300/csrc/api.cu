@@ -11,6 +11,7 @@
 
 int rbffd_init_device(mm_ctx *ctx);
 int batched_init_device(mm_ctx *ctx);
+int mlp_init_device(mm_ctx *ctx);
 
 int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...) {
     if (ctx) {
@@ -128,7 +129,8 @@ int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream) {
     }
     ctx->num_sms = sms;
     ctx->smem_optin = (size_t)optin;
-    if (rbffd_init_device(ctx) != MM_OK || batched_init_device(ctx) != MM_OK) {
+    if (rbffd_init_device(ctx) != MM_OK || batched_init_device(ctx) != MM_OK ||
+        mlp_init_device(ctx) != MM_OK) {
         delete ctx;
         return MM_ECUDA;
     }

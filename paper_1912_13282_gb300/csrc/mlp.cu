@@ -1,0 +1,964 @@
+// Learned surrogate of the Laplacian stencil weights (no counterpart in the
+// paper): a GELU multilayer perceptron 2n -> 256 -> 256 -> 256 -> n on the
+// scaled stencil offsets, BF16 weights/activations with FP32 accumulation on
+// the tensor cores (mma.sync m16n8k16), trained on weights the method itself
+// produces.  Its predictions are projected in FP64 onto the monomial rows
+// Q^T w = l_q of the augmented system (Section 2.2.2, eq. rbf-system-aug), then
+// judged by the remaining rows' residual; rejected stencils get the FP64 solve.
+//
+// Layout: feature width padded to 64, outputs to 32 (zero weights and inputs in
+// the padding), hidden width 256, 3 hidden layers.  Parameters are FP32
+// "master" copies updated by Adam, with BF16 copies for the GEMMs.
+#include <cuda_bf16.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <random>
+#include <vector>
+
+#include "rbffd_dev.cuh"
+
+struct mm_mlp {
+    int device = 0;
+    int n_in = 0, n_out = 0, H = 256, L = 3;
+    static constexpr int KIN = 64, KOUT = 32;   // padded widths
+    int64_t bmax = 0;                           // rows per internal batch
+    int step = 0;
+    // device buffers
+    float *p = nullptr, *g = nullptr, *am = nullptr, *av = nullptr;   // padded layout
+    __nv_bfloat16 *wb = nullptr;                                       // bf16 weights
+    float *Z = nullptr;                 // [3][bmax][256] pre-activations
+    __nv_bfloat16 *Hb = nullptr;        // [3][bmax][256] activations
+    __nv_bfloat16 *Xb = nullptr;        // [bmax][64]
+    float *Y = nullptr;                 // [bmax][32]
+    __nv_bfloat16 *dY = nullptr;        // [bmax][32]
+    __nv_bfloat16 *dZa = nullptr, *dZb = nullptr;   // [bmax][256]
+    float *loss = nullptr;              // [1]
+    float *ymean = nullptr, *ystd = nullptr;   // [32] output scaling (device)
+    std::vector<float> h_mean, h_std;
+    int64_t np_pad = 0;
+    // offsets into the padded parameter vector
+    int64_t oW[4], ob[4];
+};
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+constexpr int kH = 256, kKIN = 64, kKOUT = 32;
+
+// ------------------------------------------------------------------ GEMM
+// C[M x N] = A[M x K] * B^T with B given as [N x K]; either operand may be
+// stored K-contiguous ([m][k]) or M-contiguous ([k][m]).  Block tile 64 x 64 x
+// 32, four warps of 32 x 32, mma.sync m16n8k16 BF16 -> FP32.  K must be a
+// multiple of 8 and ld* multiples of 8 (16-byte vector loads); M, N arbitrary.
+constexpr int BM = 64, BN = 64, BK = 32, SPAD = 8;
+
+enum Epi { EPI_ATOMIC_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2, EPI_DGELU = 3 };
+
+struct EpiParams {
+    float *c;  int ldc; float alpha;   // EPI_ATOMIC_F32 / EPI_BIAS_F32 output
+    const float *bias;                 // bias[n]
+    float *z;  int ldz;                // pre-activation (EPI_BIAS_GELU writes, EPI_DGELU reads)
+    bf16 *h;   int ldh;                // bf16 output (activation or dZ)
+};
+
+__device__ __forceinline__ float gelu_f(float z) {
+    const float c = 0.7978845608028654f;
+    return 0.5f * z * (1.0f + tanhf(c * (z + 0.044715f * z * z * z)));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    const float c = 0.7978845608028654f;
+    const float t = tanhf(c * (z + 0.044715f * z * z * z));
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * z * z);
+}
+
+template <bool KMAJ>
+__device__ __forceinline__ void load_tile(bf16 (*S)[BK + SPAD], const bf16 *G, int ld, int r0, int k0,
+                                          int R, int K) {
+    const int tid = threadIdx.x;
+    if (KMAJ) {
+        // 64 rows x 32 k: 256 vectors of 8
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int v = tid + 128 * j, r = v >> 2, kc = (v & 3) * 8;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (r0 + r < R && k0 + kc < K) val = *reinterpret_cast<const uint4 *>(G + (int64_t)(r0 + r) * ld + k0 + kc);
+            *reinterpret_cast<uint4 *>(&S[r][kc]) = val;
+        }
+    } else {
+        // stored [k][r]: 32 k x 64 r, vectors of 8 along r, written transposed
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int v = tid + 128 * j, k = v >> 3, rc = (v & 7) * 8;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            const bool inb = k0 + k < K && r0 + rc < R;
+            if (inb && r0 + rc + 8 <= R) val = *reinterpret_cast<const uint4 *>(G + (int64_t)(k0 + k) * ld + r0 + rc);
+            const bf16 *e = reinterpret_cast<const bf16 *>(&val);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                bf16 x = e[i];
+                if (inb && r0 + rc + 8 > R) x = (r0 + rc + i < R) ? G[(int64_t)(k0 + k) * ld + r0 + rc + i] : __float2bfloat16(0.f);
+                S[rc + i][k] = x;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool AK, bool BKM, int EPI>
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *A, int lda,
+                                              const bf16 *B, int ldb, EpiParams ep, int kslice) {
+    __shared__ __align__(16) bf16 As[BM][BK + SPAD];
+    __shared__ __align__(16) bf16 Bs[BN][BK + SPAD];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        load_tile<AK>(As, A, lda, m0, k0, M, ke);
+        load_tile<BKM>(Bs, B, ldb, n0, k0, N, ke);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm * 32 + mt * 16 + g;
+                af[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
+                af[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
+                af[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t + 8]);
+                af[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = wn * 32 + nt * 8 + g;
+                bfr[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * t]);
+                bfr[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma16816(acc[mt][nt], af[mt], bfr[nt]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int r = m0 + wm * 32 + mt * 16 + g + 8 * h;
+                    const int c = n0 + wn * 32 + nt * 8 + 2 * t + q;
+                    if (r >= M || c >= N) continue;
+                    const float v = acc[mt][nt][2 * h + q];
+                    if (EPI == EPI_ATOMIC_F32) {
+                        atomicAdd(&ep.c[(int64_t)r * ep.ldc + c], ep.alpha * v);
+                    } else if (EPI == EPI_BIAS_GELU) {
+                        const float z = v + ep.bias[c];
+                        ep.z[(int64_t)r * ep.ldz + c] = z;
+                        ep.h[(int64_t)r * ep.ldh + c] = __float2bfloat16(gelu_f(z));
+                    } else if (EPI == EPI_BIAS_F32) {
+                        ep.c[(int64_t)r * ep.ldc + c] = v + ep.bias[c];
+                    } else {
+                        const float z = ep.z[(int64_t)r * ep.ldz + c];
+                        ep.h[(int64_t)r * ep.ldh + c] = __float2bfloat16(v * gelu_grad_f(z));
+                    }
+                }
+}
+
+template <bool AK, bool BKM, int EPI>
+int gemm(mm_ctx *ctx, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
+         const EpiParams &ep, int splits = 1) {
+    const int kslice = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (K + kslice - 1) / kslice);
+    k_gemm<AK, BKM, EPI><<<grid, 128, 0, ctx->stream>>>(M, N, K, A, lda, B, ldb, ep, kslice);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+// ------------------------------------------------------------ elementwise
+__global__ void k_pack_x(const float *x, int64_t B, int n_in, bf16 *xb) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * kKIN;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / kKIN;
+        const int c = (int)(i % kKIN);
+        xb[i] = __float2bfloat16(c < n_in ? x[r * n_in + c] : 0.f);
+    }
+}
+
+// dY = 2 (Y - (T - mean)/std) / (B n_out) on the n_out real columns (0 in the
+// padding); loss += mean squared normalised error.
+__global__ void k_loss(const float *Y, const float *T, int64_t B, int n_out, const float *mean,
+                       const float *std, bf16 *dY, float *loss) {
+    float s = 0.f;
+    const float scale = 2.0f / ((float)B * n_out);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * kKOUT;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / kKOUT;
+        const int c = (int)(i % kKOUT);
+        float d = 0.f;
+        if (c < n_out) {
+            const float t = (T[r * n_out + c] - mean[c]) / std[c];
+            const float e = Y[i] - t;
+            d = scale * e;
+            s += e * e;
+        }
+        dY[i] = __float2bfloat16(d);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, s / ((float)B * n_out));
+}
+
+// db[c] += sum_r dZ[r][c] (columns across threads, rows across blocks)
+__global__ void k_bias_grad(const bf16 *dZ, int64_t B, int N, float *db) {
+    const int c = threadIdx.x;
+    if (c >= N) return;
+    float s = 0.f;
+    for (int64_t r = blockIdx.x; r < B; r += gridDim.x) s += __bfloat162float(dZ[r * N + c]);
+    atomicAdd(&db[c], s);
+}
+
+// Adam (Kingma & Ba) on the FP32 master copy; refreshes the BF16 weights.
+__global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t np, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of the four weight matrices (not the biases).
+__global__ void k_refresh_bf16(const float *p, bf16 *wb, int64_t o1, int64_t n1, int64_t o2, int64_t n2,
+                               int64_t o3, int64_t n3, int64_t o4, int64_t n4) {
+    const int64_t tot = n1 + n2 + n3 + n4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t src;
+        if (i < n1) src = o1 + i;
+        else if (i < n1 + n2) src = o2 + (i - n1);
+        else if (i < n1 + n2 + n3) src = o3 + (i - n1 - n2);
+        else src = o4 + (i - n1 - n2 - n3);
+        wb[i] = __float2bfloat16(p[src]);
+    }
+}
+
+__global__ void k_denorm(const float *Y, int64_t B, int n_out, const float *mean, const float *std,
+                         float *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * n_out;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n_out;
+        const int c = (int)(i % n_out);
+        out[i] = Y[r * kKOUT + c] * std[c] + mean[c];
+    }
+}
+
+int grid1(mm_ctx *ctx, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
+}
+
+// bf16 weight matrix i (0..3) inside wb
+const bf16 *wmat(const mm_mlp *net, int i) {
+    int64_t off = 0;
+    const int64_t sz[4] = {(int64_t)kH * kKIN, (int64_t)kH * kH, (int64_t)kH * kH, (int64_t)kKOUT * kH};
+    for (int j = 0; j < i; ++j) off += sz[j];
+    return net->wb + off;
+}
+
+// Forward pass of `B` rows already packed in net->Xb; output in net->Y.
+int forward(mm_ctx *ctx, mm_mlp *net, int64_t B) {
+    EpiParams ep{};
+    const bf16 *in = net->Xb;
+    int kin = kKIN;
+    for (int l = 0; l < 3; ++l) {
+        ep.bias = net->p + net->ob[l];
+        ep.z = net->Z + (int64_t)l * net->bmax * kH;
+        ep.ldz = kH;
+        ep.h = net->Hb + (int64_t)l * net->bmax * kH;
+        ep.ldh = kH;
+        int rc = gemm<true, true, EPI_BIAS_GELU>(ctx, (int)B, kH, kin, in, kin, wmat(net, l), kin, ep);
+        if (rc != MM_OK) return rc;
+        in = ep.h;
+        kin = kH;
+    }
+    EpiParams eo{};
+    eo.c = net->Y;
+    eo.ldc = kKOUT;
+    eo.bias = net->p + net->ob[3];
+    return gemm<true, true, EPI_BIAS_F32>(ctx, (int)B, kKOUT, kH, in, kH, wmat(net, 3), kH, eo);
+}
+
+// Gradients of the mean squared error w.r.t. all parameters into net->g
+// (zeroed here), for B rows with targets T (raw, [B x n_out]).
+int backward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *T) {
+    cudaStream_t st = ctx->stream;
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(net->g, 0, sizeof(float) * net->np_pad, st));
+    k_loss<<<grid1(ctx, B * kKOUT), 256, 0, st>>>(net->Y, T, B, net->n_out, net->ymean, net->ystd,
+                                                   net->dY, net->loss);
+    MM_LAUNCH_CHECK(ctx);
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
+    // output layer
+    const bf16 *H3 = net->Hb + 2 * net->bmax * kH;
+    EpiParams e{};
+    e.c = net->g + net->oW[3]; e.ldc = kH; e.alpha = 1.f;
+    int rc = gemm<false, false, EPI_ATOMIC_F32>(ctx, kKOUT, kH, (int)B, net->dY, kKOUT, H3, kH, e, splits);
+    if (rc) return rc;
+    k_bias_grad<<<std::min<int64_t>(B, 1024), kKOUT, 0, st>>>(net->dY, B, kKOUT, net->g + net->ob[3]);
+    EpiParams ed{};
+    ed.z = net->Z + 2 * net->bmax * kH; ed.ldz = kH; ed.h = net->dZa; ed.ldh = kH;
+    rc = gemm<true, false, EPI_DGELU>(ctx, (int)B, kH, kKOUT, net->dY, kKOUT, wmat(net, 3), kH, ed);
+    if (rc) return rc;
+    bf16 *dZ = net->dZa, *dZn = net->dZb;
+    for (int l = 2; l >= 0; --l) {
+        const bf16 *Hin = l == 0 ? net->Xb : net->Hb + (int64_t)(l - 1) * net->bmax * kH;
+        const int kin = l == 0 ? kKIN : kH;
+        EpiParams ew{};
+        ew.c = net->g + net->oW[l]; ew.ldc = kin; ew.alpha = 1.f;
+        rc = gemm<false, false, EPI_ATOMIC_F32>(ctx, kH, kin, (int)B, dZ, kH, Hin, kin, ew, splits);
+        if (rc) return rc;
+        k_bias_grad<<<std::min<int64_t>(B, 1024), kH, 0, st>>>(dZ, B, kH, net->g + net->ob[l]);
+        MM_LAUNCH_CHECK(ctx);
+        if (l > 0) {
+            EpiParams eg{};
+            eg.z = net->Z + (int64_t)(l - 1) * net->bmax * kH; eg.ldz = kH; eg.h = dZn; eg.ldh = kH;
+            rc = gemm<true, false, EPI_DGELU>(ctx, (int)B, kH, kH, dZ, kH, wmat(net, l), kH, eg);
+            if (rc) return rc;
+            std::swap(dZ, dZn);
+        }
+    }
+    return MM_OK;
+}
+
+int refresh_bf16(mm_ctx *ctx, mm_mlp *net) {
+    const int64_t n1 = (int64_t)kH * kKIN, n2 = (int64_t)kH * kH, n4 = (int64_t)kKOUT * kH;
+    k_refresh_bf16<<<grid1(ctx, n1 + 2 * n2 + n4), 256, 0, ctx->stream>>>(
+        net->p, net->wb, net->oW[0], n1, net->oW[1], n2, net->oW[2], n2, net->oW[3], n4);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+// ------------------------------------------------------ stencil features
+// Scaled offsets xi_j = (x_j - x_c)/s, s = max distance, of the n stencil nodes
+// in stencil order: feature row [xi_0x, xi_0y, xi_1x, ...] (FP32).
+template <int DIM>
+__global__ void k_features(const double *pts, const int64_t *rp, const int32_t *col, int64_t r0,
+                           int64_t r1, int n, float *x, double *scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = r0 + gw; row < r1; row += nw) {
+        const int64_t b = rp[row];
+        double d[DIM] = {};
+        double r2 = 0.0;
+        if (lane < n) {
+            const int j = col[b + lane];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                d[a] = pts[(int64_t)j * DIM + a] - pts[row * DIM + a];
+                r2 = fma(d[a], d[a], r2);
+            }
+        }
+        for (int o = 16; o; o >>= 1) r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+        const double s = sqrt(r2);
+        if (lane < n) {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) x[(row - r0) * (int64_t)n * DIM + lane * DIM + a] = (float)(d[a] / s);
+        }
+        if (lane == 0 && scale) scale[row - r0] = s;
+    }
+}
+
+// ------------------------------------------------- projection and judge
+// One warp per stencil (n <= 32, l <= 32).  wt: predicted scaled Laplacian
+// weights [n] (FP32).  Least-norm correction onto Q^T w = l_q:
+//     w = wt + Q z,  (Q^T Q) z = l_q - Q^T wt,
+// solved with an FP32 Cholesky of the Jacobi-scaled Gram matrix and FP64
+// constraint residuals (up to 4 passes, until the rows hold to 1e-15 relative).
+// Judge: r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least squares),
+// rho = ||r - Q lambda||_inf / ||l_phi||_inf; accept if rho <= tau (FP32).
+struct ProjParams {
+    WParams P;              // LAP only, k, m, row range, output vals[0]
+    const float *wt;        // [rows x n] predictions (scaled units), row - row_begin
+    float tau;
+    int *fb_list, *fb_count;
+    float *rho_out;         // optional [rows]
+};
+
+// Cholesky-based solve of (D G D) v = rhs in place (lane 0; l <= 16).
+__device__ void chol_solve(const float (*Lg)[17], float *v, int l) {
+    for (int i = 0; i < l; ++i) {
+        float t = v[i];
+        for (int j = 0; j < i; ++j) t -= Lg[i][j] * v[j];
+        v[i] = t / Lg[i][i];
+    }
+    for (int i = l - 1; i >= 0; --i) {
+        float t = v[i];
+        for (int j = i + 1; j < l; ++j) t -= Lg[j][i] * v[j];
+        v[i] = t / Lg[i][i];
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjParams J) {
+    constexpr int NM = 32, LM = 16;
+    const WParams &P = J.P;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ double s_xi[4][NM * DIM];
+    __shared__ float s_xi32[4][NM * DIM];
+    __shared__ double s_Q[4][NM][LM + 1];
+    __shared__ float s_Q32[4][NM][LM + 1];
+    __shared__ float s_G[4][LM][LM + 1];
+    __shared__ double s_w[4][NM];
+    __shared__ float s_w32[4][NM], s_r[4][NM];
+    __shared__ float s_v[4][LM], s_d[4][LM];
+    double *xi = s_xi[wib];
+    float *x32 = s_xi32[wib];
+    const int l = P.l, di = DIM - 2, k = P.k;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = P.row_begin + gw; row < P.row_end; row += nw) {
+        int n;
+        int64_t rb;
+        double s;
+        if (!load_stencil<DIM>(P, row, n, rb, xi, s) || n > NM || l > LM) {
+            reject_row(P, row, rb, n, MM_ST_BADARG);
+            __syncwarp();
+            continue;
+        }
+        // Q by stencil node (FP64 and FP32), predicted weights
+        if (lane < n) {
+            double *Qj = s_Q[wib][lane];
+            float *Qf = s_Q32[wib][lane];
+            Qj[0] = 1.0;
+            Qf[0] = 1.0f;
+            for (int b = 1; b < l; ++b) {
+                const double v = Qj[c_mono.parent[di][b]] * xi[lane * DIM + c_mono.var[di][b]];
+                Qj[b] = v;
+                Qf[b] = (float)v;
+            }
+            for (int a = 0; a < DIM; ++a) x32[lane * DIM + a] = (float)xi[lane * DIM + a];
+            s_w[wib][lane] = (double)J.wt[(row - P.row_begin) * n + lane];
+        }
+        __syncwarp();
+        // Gram matrix Q^T Q (FP32), Jacobi scaling D = diag(G)^-1/2, Cholesky D G D = L L^T
+        for (int e = lane; e < l * l; e += 32) {
+            const int a = e / l, b = e % l;
+            float acc = 0.f;
+            for (int j = 0; j < n; ++j) acc = fmaf(s_Q32[wib][j][a], s_Q32[wib][j][b], acc);
+            s_G[wib][a][b] = acc;
+        }
+        __syncwarp();
+        if (lane < l) s_d[wib][lane] = rsqrtf(fmaxf(s_G[wib][lane][lane], 1e-30f));
+        __syncwarp();
+        for (int e = lane; e < l * l; e += 32) {
+            const int a = e / l, b = e % l;
+            s_G[wib][a][b] *= s_d[wib][a] * s_d[wib][b];
+        }
+        __syncwarp();
+        bool ok = true;
+        for (int c = 0; c < l; ++c) {
+            const float dcc = s_G[wib][c][c];
+            ok &= dcc > 0.f;
+            const float ld = sqrtf(fmaxf(dcc, 1e-30f));
+            __syncwarp();
+            if (lane > c && lane < l) s_G[wib][lane][c] /= ld;
+            if (lane == 0) s_G[wib][c][c] = ld;
+            __syncwarp();
+            const int w = l - c - 1;
+            for (int e = lane; e < w * w; e += 32) {
+                const int i = c + 1 + e / w, j = c + 1 + e % w;
+                if (j <= i) s_G[wib][i][j] -= s_G[wib][i][c] * s_G[wib][j][c];
+            }
+            __syncwarp();
+        }
+        // FP64 constraint residual c = l_q - Q^T w, FP32 correction w += Q D (DGD)^-1 D c
+        for (int pass = 0; pass < 4; ++pass) {
+            double cb = 0.0, sc = 0.0;
+            if (lane < l) {
+                cb = (double)c_mono.lap[di][lane];
+                for (int j = 0; j < n; ++j) {
+                    const double t = s_Q[wib][j][lane] * s_w[wib][j];
+                    cb -= t;
+                    sc += fabs(t);
+                }
+            }
+            double cm = fabs(cb) / fmax(1.0, sc);
+            for (int o = 16; o; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+            if (cm <= 1e-15) break;
+            if (lane < l) s_v[wib][lane] = (float)cb * s_d[wib][lane];
+            __syncwarp();
+            if (lane == 0) chol_solve(s_G[wib], s_v[wib], l);
+            __syncwarp();
+            if (lane < n) {
+                // FP64, so w - wt stays in range(Q) to FP64 rounding (the exact
+                // least-norm correction)
+                double corr = 0.0;
+                for (int b = 0; b < l; ++b) corr = fma(s_Q[wib][lane][b], (double)(s_v[wib][b] * s_d[wib][b]), corr);
+                s_w[wib][lane] += corr;
+            }
+            __syncwarp();
+        }
+        // judge (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r, e = r - Q lambda
+        if (lane < n) s_w32[wib][lane] = (float)s_w[wib][lane];
+        __syncwarp();
+        float lphi = 0.f;
+        if (lane < n) {
+            float r2 = 0.f;
+            for (int a = 0; a < DIM; ++a) r2 = fmaf(x32[lane * DIM + a], x32[lane * DIM + a], r2);
+            float rk2 = sqrtf(r2);
+            for (int i = 3; i < k; i += 2) rk2 *= r2;
+            lphi = (float)(k * (k + DIM - 2)) * rk2;
+            float aw = 0.f;
+            for (int j = 0; j < n; ++j) {
+                float d2 = 0.f;
+                for (int a = 0; a < DIM; ++a) {
+                    const float t = x32[lane * DIM + a] - x32[j * DIM + a];
+                    d2 = fmaf(t, t, d2);
+                }
+                float pw = sqrtf(d2);
+                for (int i = 1; i < k; i += 2) pw *= d2;
+                aw = fmaf(pw, s_w32[wib][j], aw);
+            }
+            s_r[wib][lane] = lphi - aw;
+        }
+        __syncwarp();
+        if (lane < l) {
+            float qr = 0.f;
+            for (int j = 0; j < n; ++j) qr = fmaf(s_Q32[wib][j][lane], s_r[wib][j], qr);
+            s_v[wib][lane] = qr * s_d[wib][lane];
+        }
+        __syncwarp();
+        if (lane == 0) chol_solve(s_G[wib], s_v[wib], l);
+        __syncwarp();
+        float e = 0.f;
+        if (lane < n) {
+            float ql = 0.f;
+            for (int b = 0; b < l; ++b) ql = fmaf(s_Q32[wib][lane][b], s_v[wib][b] * s_d[wib][b], ql);
+            e = fabsf(s_r[wib][lane] - ql);
+        }
+        float emax = e, lmax = fabsf(lphi);
+        for (int o = 16; o; o >>= 1) {
+            emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        }
+        const float rho = emax / fmaxf(lmax, 1e-30f);
+        const bool accept = __all_sync(0xffffffffu, ok) && rho <= J.tau && !isnan(rho);
+        if (J.rho_out && lane == 0) J.rho_out[row - P.row_begin] = rho;
+        if (accept) {
+            const double inv2 = 1.0 / (s * s);
+            if (lane < n) P.vals[0][rb + lane] = s_w[wib][lane] * inv2;
+            if (P.status && lane == 0) P.status[row] = MM_ST_ACCEPTED;
+        } else if (lane == 0) {
+            const int slot = atomicAdd(J.fb_count, 1);
+            J.fb_list[slot] = (int)row;
+            if (P.status) P.status[row] = MM_ST_NONCONVERGED;
+        }
+        __syncwarp();
+    }
+}
+
+// the FP64 solver for stencils the judge rejected
+template <int DIM>
+__global__ void __launch_bounds__(128) k_surrogate_fallback(WParams P) {
+    extern __shared__ double smem[];
+    const int wib = threadIdx.x >> 5;
+    double *base = smem + (size_t)wib * fp64_warp_doubles(P.M_max, P.pitch64, P.n_max, DIM);
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t count = *P.list_count;
+    for (int64_t t = gw; t < count; t += nw) fp64_row<DIM>(P, (int64_t)P.list[t], base, true);
+}
+
+// padded parameter layout <-> the plain layout W1 [H x n_in], b1, W2, b2, W3,
+// b3, W4 [n_out x H], b4 (row-major [out][in])
+void plain_to_padded(const mm_mlp *net, const float *plain, std::vector<float> &pad) {
+    pad.assign((size_t)net->np_pad, 0.f);
+    const float *q = plain;
+    const int ins[4] = {net->n_in, kH, kH, kH}, outs[4] = {kH, kH, kH, net->n_out};
+    const int pins[4] = {kKIN, kH, kH, kH};
+    for (int l = 0; l < 4; ++l) {
+        for (int o = 0; o < outs[l]; ++o)
+            for (int i = 0; i < ins[l]; ++i) pad[net->oW[l] + (int64_t)o * pins[l] + i] = *q++;
+        for (int o = 0; o < outs[l]; ++o) pad[net->ob[l] + o] = *q++;
+    }
+}
+
+void padded_to_plain(const mm_mlp *net, const float *pad, float *plain) {
+    float *q = plain;
+    const int ins[4] = {net->n_in, kH, kH, kH}, outs[4] = {kH, kH, kH, net->n_out};
+    const int pins[4] = {kKIN, kH, kH, kH};
+    for (int l = 0; l < 4; ++l) {
+        for (int o = 0; o < outs[l]; ++o)
+            for (int i = 0; i < ins[l]; ++i) *q++ = pad[net->oW[l] + (int64_t)o * pins[l] + i];
+        for (int o = 0; o < outs[l]; ++o) *q++ = pad[net->ob[l] + o];
+    }
+}
+
+int64_t plain_count(int n_in, int n_out) {
+    return (int64_t)kH * n_in + kH + 2 * ((int64_t)kH * kH + kH) + (int64_t)n_out * kH + n_out;
+}
+
+}  // namespace
+
+int mlp_init_device(mm_ctx *ctx) {
+    MonoTable t;
+    mono_table_host(t);
+    MM_CUDA_CHECK(ctx, cudaMemcpyToSymbol(c_mono, &t, sizeof(t)));
+    return MM_OK;
+}
+
+extern "C" {
+
+int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers, int n_out,
+                  uint64_t seed) {
+    if (!ctx || !out) return MM_EBADARG;
+    ctx->err.clear();
+    *out = nullptr;
+    if (hidden != kH || n_layers != 3 || n_in < 1 || n_in > kKIN || n_out < 1 || n_out > kKOUT)
+        return mm_fail(ctx, MM_EUNSUPPORTED, "this build supports 3 hidden layers of 256, n_in <= 64, n_out <= 32");
+    DeviceGuard g(ctx);
+    mm_mlp *net = new mm_mlp();
+    net->device = ctx->device;
+    net->n_in = n_in;
+    net->n_out = n_out;
+    net->bmax = 65536;
+    int64_t off = 0;
+    const int64_t wsz[4] = {(int64_t)kH * kKIN, (int64_t)kH * kH, (int64_t)kH * kH, (int64_t)kKOUT * kH};
+    const int64_t bsz[4] = {kH, kH, kH, kKOUT};
+    for (int l = 0; l < 4; ++l) {
+        net->oW[l] = off;
+        off += wsz[l];
+        net->ob[l] = off;
+        off += bsz[l];
+    }
+    net->np_pad = off;
+    const int64_t B = net->bmax;
+    size_t bytes_f = sizeof(float) * (size_t)(4 * off + 3 * B * kH + B * kKOUT + 1 + 2 * kKOUT);
+    size_t bytes_h = sizeof(bf16) * (size_t)(wsz[0] + wsz[1] + wsz[2] + wsz[3] + 3 * B * kH + B * kKIN +
+                                             B * kKOUT + 2 * B * kH);
+    char *fb = nullptr, *hb = nullptr;
+    if (cudaMalloc(&fb, bytes_f) != cudaSuccess || cudaMalloc(&hb, bytes_h) != cudaSuccess) {
+        cudaGetLastError();
+        if (fb) cudaFree(fb);
+        delete net;
+        return mm_fail(ctx, MM_ENOMEM, "MLP buffers");
+    }
+    float *f = (float *)fb;
+    net->p = f; f += off;
+    net->g = f; f += off;
+    net->am = f; f += off;
+    net->av = f; f += off;
+    net->Z = f; f += 3 * B * kH;
+    net->Y = f; f += B * kKOUT;
+    net->loss = f; f += 1;
+    net->ymean = f; f += kKOUT;
+    net->ystd = f;
+    bf16 *h = (bf16 *)hb;
+    net->wb = h; h += wsz[0] + wsz[1] + wsz[2] + wsz[3];
+    net->Hb = h; h += 3 * B * kH;
+    net->Xb = h; h += B * kKIN;
+    net->dY = h; h += B * kKOUT;
+    net->dZa = h; h += B * kH;
+    net->dZb = h;
+    // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases (plain layout)
+    std::mt19937_64 rng(seed);
+    std::vector<float> plain((size_t)plain_count(n_in, n_out));
+    {
+        float *q = plain.data();
+        const int ins[4] = {n_in, kH, kH, kH}, outs[4] = {kH, kH, kH, n_out};
+        for (int l = 0; l < 4; ++l) {
+            std::uniform_real_distribution<float> U(-1.f / std::sqrt((float)ins[l]), 1.f / std::sqrt((float)ins[l]));
+            for (int64_t i = 0; i < (int64_t)outs[l] * ins[l]; ++i) *q++ = U(rng);
+            for (int o = 0; o < outs[l]; ++o) *q++ = 0.f;
+        }
+    }
+    std::vector<float> pad;
+    plain_to_padded(net, plain.data(), pad);
+    net->h_mean.assign(kKOUT, 0.f);
+    net->h_std.assign(kKOUT, 1.f);
+    cudaError_t e = cudaMemcpy(net->p, pad.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(net->am, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(net->av, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemcpy(net->ymean, net->h_mean.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(net->ystd, net->h_std.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(fb);
+        cudaFree(hb);
+        delete net;
+        return mm_fail(ctx, MM_ECUDA, "MLP init: %s", cudaGetErrorString(e));
+    }
+    int rc = refresh_bf16(ctx, net);
+    if (rc == MM_OK) rc = cudaStreamSynchronize(ctx->stream) == cudaSuccess ? MM_OK : MM_ECUDA;
+    if (rc != MM_OK) {
+        cudaFree(fb);
+        cudaFree(hb);
+        delete net;
+        return rc;
+    }
+    *out = net;
+    return MM_OK;
+}
+
+void mm_mlp_destroy(mm_mlp *net) {
+    if (!net) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(net->device);
+    cudaDeviceSynchronize();
+    cudaFree(net->p);
+    cudaFree(net->wb);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete net;
+}
+
+int64_t mm_mlp_num_params(const mm_mlp *net) { return net ? plain_count(net->n_in, net->n_out) : -1; }
+
+int mm_mlp_set_params(mm_ctx *ctx, mm_mlp *net, const float *h_params) {
+    if (!ctx || !net || !h_params) return MM_EBADARG;
+    DeviceGuard g(ctx);
+    std::vector<float> pad;
+    plain_to_padded(net, h_params, pad);
+    MM_CUDA_CHECK(ctx, cudaMemcpyAsync(net->p, pad.data(), sizeof(float) * pad.size(), cudaMemcpyHostToDevice, ctx->stream));
+    int rc = refresh_bf16(ctx, net);
+    if (rc != MM_OK) return rc;
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_mlp_get_params(mm_ctx *ctx, const mm_mlp *net, float *h_params) {
+    if (!ctx || !net || !h_params) return MM_EBADARG;
+    DeviceGuard g(ctx);
+    std::vector<float> pad((size_t)net->np_pad);
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(pad.data(), net->p, sizeof(float) * pad.size(), cudaMemcpyDeviceToHost));
+    padded_to_plain(net, pad.data(), h_params);
+    return MM_OK;
+}
+
+int mm_mlp_set_output_scaling(mm_ctx *ctx, mm_mlp *net, const float *h_mean, const float *h_std) {
+    if (!ctx || !net || !h_mean || !h_std) return MM_EBADARG;
+    DeviceGuard g(ctx);
+    for (int c = 0; c < net->n_out; ++c) {
+        if (!(h_std[c] > 0)) return mm_fail(ctx, MM_EBADARG, "output scale must be > 0");
+        net->h_mean[c] = h_mean[c];
+        net->h_std[c] = h_std[c];
+    }
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->ymean, net->h_mean.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->ystd, net->h_std.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice));
+    return MM_OK;
+}
+
+int mm_mlp_forward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, float *d_y) {
+    if (!ctx || !net || B < 0 || (B > 0 && (!d_x || !d_y))) return MM_EBADARG;
+    ctx->err.clear();
+    DeviceGuard g(ctx);
+    for (int64_t b0 = 0; b0 < B; b0 += net->bmax) {
+        const int64_t bs = std::min(net->bmax, B - b0);
+        k_pack_x<<<grid1(ctx, bs * kKIN), 256, 0, ctx->stream>>>(d_x + b0 * net->n_in, bs, net->n_in, net->Xb);
+        MM_LAUNCH_CHECK(ctx);
+        int rc = forward(ctx, net, bs);
+        if (rc != MM_OK) return rc;
+        k_denorm<<<grid1(ctx, bs * net->n_out), 256, 0, ctx->stream>>>(net->Y, bs, net->n_out, net->ymean,
+                                                                        net->ystd, d_y + b0 * net->n_out);
+        MM_LAUNCH_CHECK(ctx);
+    }
+    return MM_OK;
+}
+
+int mm_mlp_grad(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, const float *d_t,
+                float *h_grads, float *h_loss) {
+    if (!ctx || !net || B < 1 || B > net->bmax || !d_x || !d_t) return MM_EBADARG;
+    ctx->err.clear();
+    DeviceGuard g(ctx);
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(net->loss, 0, sizeof(float), ctx->stream));
+    k_pack_x<<<grid1(ctx, B * kKIN), 256, 0, ctx->stream>>>(d_x, B, net->n_in, net->Xb);
+    MM_LAUNCH_CHECK(ctx);
+    int rc = forward(ctx, net, B);
+    if (rc == MM_OK) rc = backward(ctx, net, B, d_t);
+    if (rc != MM_OK) return rc;
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h_grads) {
+        std::vector<float> pad((size_t)net->np_pad);
+        MM_CUDA_CHECK(ctx, cudaMemcpy(pad.data(), net->g, sizeof(float) * pad.size(), cudaMemcpyDeviceToHost));
+        padded_to_plain(net, pad.data(), h_grads);
+    }
+    if (h_loss) MM_CUDA_CHECK(ctx, cudaMemcpy(h_loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return MM_OK;
+}
+
+int mm_mlp_train_step(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, const float *d_t,
+                      float lr, float *d_loss) {
+    if (!ctx || !net || B < 1 || B > net->bmax || !d_x || !d_t || !(lr > 0)) return MM_EBADARG;
+    ctx->err.clear();
+    DeviceGuard g(ctx);
+    cudaStream_t st = ctx->stream;
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(net->loss, 0, sizeof(float), st));
+    k_pack_x<<<grid1(ctx, B * kKIN), 256, 0, st>>>(d_x, B, net->n_in, net->Xb);
+    MM_LAUNCH_CHECK(ctx);
+    int rc = forward(ctx, net, B);
+    if (rc == MM_OK) rc = backward(ctx, net, B, d_t);
+    if (rc != MM_OK) return rc;
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)net->step), c2 = 1.f - powf(b2, (float)net->step);
+    k_adam<<<grid1(ctx, net->np_pad), 256, 0, st>>>(net->p, net->g, net->am, net->av, net->np_pad, lr, b1, b2,
+                                                     1e-8f, c1, c2);
+    MM_LAUNCH_CHECK(ctx);
+    rc = refresh_bf16(ctx, net);
+    if (rc != MM_OK) return rc;
+    if (d_loss) MM_CUDA_CHECK(ctx, cudaMemcpyAsync(d_loss, net->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return MM_OK;
+}
+
+int mm_mlp_save(mm_ctx *ctx, const mm_mlp *net, const char *path) {
+    if (!ctx || !net || !path) return MM_EBADARG;
+    DeviceGuard g(ctx);
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<float> buf((size_t)(3 * net->np_pad));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(buf.data(), net->p, sizeof(float) * net->np_pad, cudaMemcpyDeviceToHost));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(buf.data() + net->np_pad, net->am, sizeof(float) * net->np_pad, cudaMemcpyDeviceToHost));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(buf.data() + 2 * net->np_pad, net->av, sizeof(float) * net->np_pad, cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) return mm_fail(ctx, MM_EBADARG, "cannot write %s", path);
+    const int hdr[6] = {0x4d4c5031 /* 'MLP1' */, net->n_in, net->H, net->L, net->n_out, net->step};
+    fwrite(hdr, sizeof hdr, 1, f);
+    fwrite(net->h_mean.data(), sizeof(float), kKOUT, f);
+    fwrite(net->h_std.data(), sizeof(float), kKOUT, f);
+    fwrite(buf.data(), sizeof(float), buf.size(), f);
+    fclose(f);
+    return MM_OK;
+}
+
+int mm_mlp_load(mm_ctx *ctx, mm_mlp *net, const char *path) {
+    if (!ctx || !net || !path) return MM_EBADARG;
+    DeviceGuard g(ctx);
+    FILE *f = fopen(path, "rb");
+    if (!f) return mm_fail(ctx, MM_EBADARG, "cannot read %s", path);
+    int hdr[6];
+    std::vector<float> mean(kKOUT), sd(kKOUT), buf((size_t)(3 * net->np_pad));
+    bool okr = fread(hdr, sizeof hdr, 1, f) == 1 && hdr[0] == 0x4d4c5031 && hdr[1] == net->n_in &&
+               hdr[2] == net->H && hdr[3] == net->L && hdr[4] == net->n_out &&
+               fread(mean.data(), sizeof(float), kKOUT, f) == (size_t)kKOUT &&
+               fread(sd.data(), sizeof(float), kKOUT, f) == (size_t)kKOUT &&
+               fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!okr) return mm_fail(ctx, MM_EBADARG, "%s is not a checkpoint of this network", path);
+    net->step = hdr[5];
+    net->h_mean = mean;
+    net->h_std = sd;
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->p, buf.data(), sizeof(float) * net->np_pad, cudaMemcpyHostToDevice));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->am, buf.data() + net->np_pad, sizeof(float) * net->np_pad, cudaMemcpyHostToDevice));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->av, buf.data() + 2 * net->np_pad, sizeof(float) * net->np_pad, cudaMemcpyHostToDevice));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->ymean, mean.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice));
+    MM_CUDA_CHECK(ctx, cudaMemcpy(net->ystd, sd.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice));
+    int rc = refresh_bf16(ctx, net);
+    if (rc == MM_OK) MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    return rc;
+}
+
+int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
+                        const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end, int n,
+                        float *d_x, double *d_scale) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if ((dim != 2 && dim != 3) || N < 1 || !d_pts || !stencils || !stencils->d_row_ptr ||
+        !stencils->d_col || row_begin < 0 || row_end < row_begin || row_end > stencils->nrows ||
+        n < 1 || n > 32 || !d_x)
+        return mm_fail(ctx, MM_EBADARG, "bad arguments");
+    DeviceGuard g(ctx);
+    const int64_t rows = row_end - row_begin;
+    if (rows == 0) return MM_OK;
+    const int blocks = (int)std::min<int64_t>((rows + 3) / 4, (int64_t)ctx->num_sms * 32);
+    if (dim == 2) k_features<2><<<blocks, 128, 0, ctx->stream>>>(d_pts, stencils->d_row_ptr, stencils->d_col, row_begin, row_end, n, d_x, d_scale);
+    else k_features<3><<<blocks, 128, 0, ctx->stream>>>(d_pts, stencils->d_row_ptr, stencils->d_col, row_begin, row_end, n, d_x, d_scale);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, int64_t N,
+                               const double *d_pts, const mm_csr_pattern *stencils,
+                               int64_t row_begin, int64_t row_end, int n, double tau,
+                               double *d_lap_vals, int32_t *d_status, float *d_rho) {
+    if (!ctx || !net) return MM_EBADARG;
+    ctx->err.clear();
+    if (dim != 2 || n * dim != net->n_in || n != net->n_out)
+        return mm_fail(ctx, MM_EBADARG, "the network expects 2D stencils of %d nodes", net->n_out);
+    if (!(tau > 0)) return mm_fail(ctx, MM_EBADARG, "tau must be > 0");
+    double *vals[1] = {d_lap_vals};
+    WeightsJob job{};
+    int rc = weights_job_from_args(ctx, MM_LAP, k, m, dim, N, d_pts, nullptr, stencils, row_begin,
+                                   row_end, n, vals, d_status, &job);
+    if (rc != MM_OK) return rc;
+    DeviceGuard g(ctx);
+    const int64_t rows = row_end - row_begin;
+    if (rows == 0) return MM_OK;
+    WParams P = wparams_from_job(ctx, job);
+    if (P.l > 16) return mm_fail(ctx, MM_EUNSUPPORTED, "surrogate projection handles l <= 16");
+    const int64_t chunk = net->bmax;
+    WsCarve wc;
+    const size_t o_x = wc.take<float>((size_t)std::min(rows, chunk) * n * dim);
+    const size_t o_y = wc.take<float>((size_t)std::min(rows, chunk) * n);
+    const size_t o_cnt = wc.take<int>(1);
+    const size_t o_list = wc.take<int>((size_t)rows);
+    char *ws = mm_workspace(ctx, wc.off);
+    if (!ws) return mm_fail(ctx, MM_ENOMEM, "surrogate workspace of %zu bytes", wc.off);
+    float *x = (float *)(ws + o_x), *y = (float *)(ws + o_y);
+    int *cnt = (int *)(ws + o_cnt), *list = (int *)(ws + o_list);
+    cudaStream_t st = ctx->stream;
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    for (int64_t r0 = row_begin; r0 < row_end; r0 += chunk) {
+        const int64_t r1 = std::min(row_end, r0 + chunk);
+        rc = mm_stencil_features(ctx, dim, N, d_pts, stencils, r0, r1, n, x, nullptr);
+        if (rc != MM_OK) return rc;
+        rc = mm_mlp_forward(ctx, net, r1 - r0, x, y);
+        if (rc != MM_OK) return rc;
+        ProjParams J{};
+        J.P = P;
+        J.P.row_begin = r0;
+        J.P.row_end = r1;
+        J.wt = y;
+        J.tau = (float)tau;
+        J.fb_list = list;
+        J.fb_count = cnt;
+        J.rho_out = d_rho ? d_rho + (r0 - row_begin) : nullptr;
+        const int blocks = (int)std::min<int64_t>((r1 - r0 + 3) / 4, (int64_t)ctx->num_sms * 32);
+        k_project<2><<<blocks, 128, 0, st>>>(J);
+        MM_LAUNCH_CHECK(ctx);
+    }
+    // rejected stencils: FP64 solve
+    WParams F = P;
+    F.list = list;
+    F.list_count = cnt;
+    const size_t w64 = fp64_warp_doubles(F.M_max, F.pitch64, F.n_max, dim) * sizeof(double);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / w64));
+    const size_t sm = w64 * wpb;
+    MM_CUDA_CHECK(ctx, mm_set_smem(ctx, (const void *)k_surrogate_fallback<2>, sm));
+    const int blocks = (int)std::min<int64_t>((rows + wpb - 1) / wpb, (int64_t)ctx->num_sms * 32);
+    k_surrogate_fallback<2><<<blocks, wpb * 32, sm, st>>>(F);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+}  // extern "C"
