@@ -1,19 +1,35 @@
-"""Benchmark: RBF-FD stencil-weight throughput (nodes/s) on the 1,000,000-node
-2D disk-with-5-holes workload (interior: 25 nearest nodes, r^5 + degree-4
-monomials, Laplacian and gradient; boundary: 30 nearest nodes, d/dn).
+"""Benchmark: RBF-FD stencil-weight throughput (nodes/s).
 
-One step = the whole hot path over the node set: grid binning + kNN stencils
-(two classes), weights for both classes in the chosen precision (FP32 LU with
-FP64 refinement, FP64 fallback), and one application of each assembled
-operator to a field.  The plain FP64 GPU path is timed the same way beside it.
+Default workload (the one the headline metric is quoted on): the 1,000,000-node
+2D unit disk minus 5 holes; interior nodes get 25-node stencils with PHS r^5 +
+degree-4 monomials (Laplacian, d/dx, d/dy), boundary nodes 30-node stencils
+with d/dn.  One step = the whole hot path over the node set: grid binning +
+kNN stencils, weights for both classes in the chosen form (FP32 LU with FP64
+refinement and FP64 fallback), one application of each assembled operator.
+The plain FP64 GPU path is timed the same way beside it; the sampled error
+against the CPU oracle and the Poisson solution error of both weight sets are
+reported with it.
+
+Other workloads (--workload):
+  ball       4,000,000-node 3D unit ball, three stencil classes (interior
+             n=35 deg 2, refined n=60 deg 3, boundary n=45 d/dn) in one
+             persistent launch with autotuned tiles.
+  batch      64 independent 2D/3D node sets (10^4..2*10^6 nodes, log-uniform),
+             all Laplacian weights + 100 explicit diffusion steps in one
+             captured CUDA graph.
+  surrogate  MLP surrogate trained on 2^20 patch stencils, evaluated on
+             10^6 held-out stencils against the FP64 and FP32+IR paths.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own
-independent node set (seed = rank): weak scaling, no data-path collective.
+                       [--workload disk|ball|batch|surrogate]
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+independent node set (seed = rank): weak scaling, no data-path collective;
+the step time is the maximum over ranks.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -28,39 +44,91 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = {
+METRIC = "stencil weights nodes/s at stated error vs FP64 oracle; chosen form vs plain FP64 GPU"
+DISK = {
     "workload": "disk minus 5 holes, 1e6 nodes: interior n=25 PHS r^5 + deg-4 monomials "
                 "(lap, dx, dy); boundary n=30 d/dn",
     "N_target": 1_000_000,
-    "interior": {"n": 25, "k": 5, "m": 4, "ops": ["lap", "dx", "dy"]},
-    "boundary": {"n": 30, "k": 5, "m": 4, "ops": ["dn"]},
+    "interior": {"n": 25, "k": 5, "m": 4, "ops": 1 | 2 | 4},
+    "boundary": {"n": 30, "k": 5, "m": 4, "ops": 16},
 }
-METRIC = "stencil weights nodes/s at stated error vs FP64 oracle; chosen form vs plain FP64 GPU"
+# kernels of one disk step: kNN (bbox, grid params, cell count, 3 scan passes,
+# scatter, 2 queries) + per class (solve, FP64 fallback) x 2 + 3 SpMV
+DISK_LAUNCHES_PER_STEP = 9 + 4 + 3
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-target", type=int, default=WORKLOAD["N_target"])
+    ap.add_argument("--workload", default="disk", choices=["disk", "ball", "batch", "surrogate"])
+    ap.add_argument("--n-target", type=int, default=None, help="override the node count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-error", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-poisson", action="store_true")
+    return ap.parse_args(argv)
 
 
-def dist_info():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+# --------------------------------------------------------------- ranks
+class Ranks:
+    """RANK / WORLD_SIZE / LOCAL_RANK from the environment, process group
+    (NCCL on GPUs, gloo for the CPU tests) when WORLD_SIZE > 1."""
+
+    def __init__(self, backend="nccl"):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device(f"cuda:{self.local}"))
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, values):
+        """Element-wise maximum of a list of floats over all ranks."""
+        if self.dist is None:
+            return [float(v) for v in values]
+        import torch
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return [float(v) for v in t.cpu()]
+
+    def sum(self, values):
+        """Element-wise sum of a list of floats over all ranks."""
+        if self.dist is None:
+            return [float(v) for v in values]
+        import torch
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return [float(v) for v in t.cpu()]
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
 
 
-# ------------------------------------------------------------------ clocks
+def throughput(units_all_ranks, ms_total_max, steps):
+    """Whole-job units/s: the units all ranks process per step, over the
+    slowest rank's time."""
+    return units_all_ranks * steps / (ms_total_max * 1e-3)
+
+
+# ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons in the background."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -112,20 +180,82 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- workload
-def make_workload(seed: int, n_target: int):
+# ------------------------------------------------------- roofline helpers
+def mixed_fp64_flops(n, l, R, dim, k, residuals=1):
+    """Algorithmic FP64 flops of the FP32+IR solve of one stencil: the FP64
+    A block (per pair: dim differences and squares, a square root, the
+    powers of r), Q, the right-hand sides, `residuals` full residuals
+    b - K x over the nonzero blocks, the constraint-row residual, and the
+    FP64 updates of x (2 flops per multiply-add)."""
+    M = n + l
+    pairs = n * (n - 1) // 2
+    a_block = pairs * (2 * dim + 1 + (k + 1) // 2)
+    q_block = n * (l - 1)
+    rhs = n * (dim + 2 + R * (dim + 1))
+    full = 2 * R * (n * M + l * n)
+    constraint = 2 * R * n * l
+    updates = M * R * (residuals + 2)
+    return a_block + q_block + rhs + residuals * full + constraint + updates
+
+
+def fp64_solve_flops(n, l, R, dim, k):
+    """Algorithmic FP64 flops of the plain solve: assembly, LU of the M x M
+    augmented matrix applied to R right-hand sides, back substitution."""
+    M = n + l
+    pairs = n * (n - 1) // 2
+    assembly = pairs * (2 * dim + 1 + (k + 1) // 2) + n * (l - 1) + n * (dim + 2 + R * (dim + 1))
+    lu = sum(2 * (M - kk - 1) * (M + R - kk - 1) + (M - kk - 1) for kk in range(M))
+    back = R * M * M
+    return assembly + lu + back
+
+
+def peaks_file():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def kernel_source_hash():
+    """Hash of the weights kernel sources, to tie a stored ncu traffic figure
+    to the kernel it was measured on."""
+    h = hashlib.sha256()
+    for f in ("rbffd_dev.cuh", "rbffd.cu"):
+        with open(os.path.join(ROOT, "paper_1912_13282_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(name):
+    """(bytes per row, source hash) stored under profiles/ for a kernel, if the
+    kernel source is unchanged since; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[name]
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+# ------------------------------------------------------------ disk workload
+def make_disk(seed: int, n_target: int):
     import nodesets as NS
     ns = NS.disk_holes(n_target, seed=seed)
     (ib, ie), (bb, be) = ns.classes["interior"], ns.classes["boundary"]
-    ni, nb = WORKLOAD["interior"]["n"], WORKLOAD["boundary"]["n"]
-    sizes = np.concatenate([np.full(ie - ib, ni), np.full(be - bb, nb)])
+    sizes = np.concatenate([np.full(ie - ib, DISK["interior"]["n"]),
+                            np.full(be - bb, DISK["boundary"]["n"])])
     rp = np.zeros(ns.N + 1, dtype=np.int64)
     np.cumsum(sizes, out=rp[1:])
     return ns, rp
 
 
-class Pipeline:
-    """Device buffers and the calls of one step."""
+class DiskPipeline:
+    """Device buffers and calls of one disk step."""
 
     def __init__(self, P, ctx, ns, rp, device):
         import torch
@@ -139,29 +269,31 @@ class Pipeline:
         self.nrm = torch.from_numpy(ns.normals).to(dv)
         self.rp = torch.from_numpy(rp).to(dv)
         self.col = torch.empty(self.nnz, dtype=torch.int32, device=dv)
-        self.op = torch.zeros(self.nnz, dtype=torch.float64, device=dv)   # lap rows + dn rows
+        # one operator array: Laplacian rows (interior) and d/dn rows (boundary)
+        self.op = torch.zeros(self.nnz, dtype=torch.float64, device=dv)
         self.dx = torch.zeros(self.nnz, dtype=torch.float64, device=dv)
         self.dy = torch.zeros(self.nnz, dtype=torch.float64, device=dv)
         self.status = torch.empty(self.N, dtype=torch.int32, device=dv)
         self.u = torch.from_numpy(np.sin(np.pi * ns.pts[:, 0]) * np.sin(np.pi * ns.pts[:, 1])).to(dv)
         self.y = torch.empty(self.N, dtype=torch.float64, device=dv)
         self.gy = torch.empty(self.N, dtype=torch.float64, device=dv)
-        ni = WORKLOAD["interior"]["n"]
-        nb = WORKLOAD["boundary"]["n"]
-        self.ranges = [(self.ib, self.ie, ni, self.col[: (self.ie - self.ib) * ni]),
+        ni, nb = DISK["interior"]["n"], DISK["boundary"]["n"]
+        self.ranges = [(self.ib, self.ie, ni, self.col[:(self.ie - self.ib) * ni]),
                        (self.bb, self.be, nb, self.col[int(rp[self.bb]):])]
 
     def knn(self):
         self.ctx.knn_stencils(self.pts, self.ranges, method=self.P.KNN_GRID)
 
-    def weights(self, precision):
-        P, W = self.P, WORKLOAD
-        wi, wb = W["interior"], W["boundary"]
-        self.ctx.rbffd_weights(P.LAP | P.DX | P.DY, wi["k"], wi["m"], self.pts, self.rp, self.col,
+    def weights_interior(self, precision):
+        wi = DISK["interior"]
+        self.ctx.rbffd_weights(wi["ops"], wi["k"], wi["m"], self.pts, self.rp, self.col,
                                [self.op, self.dx, self.dy], row_begin=self.ib, row_end=self.ie,
                                n_max=wi["n"], precision=precision, normals=self.nrm,
                                status=self.status)
-        self.ctx.rbffd_weights(P.DN, wb["k"], wb["m"], self.pts, self.rp, self.col, [self.op],
+
+    def weights_boundary(self, precision):
+        wb = DISK["boundary"]
+        self.ctx.rbffd_weights(wb["ops"], wb["k"], wb["m"], self.pts, self.rp, self.col, [self.op],
                                row_begin=self.bb, row_end=self.be, n_max=wb["n"],
                                precision=precision, normals=self.nrm, status=self.status)
 
@@ -172,69 +304,71 @@ class Pipeline:
 
     def step(self, precision):
         self.knn()
-        self.weights(precision)
+        self.weights_interior(precision)
+        self.weights_boundary(precision)
         self.apply()
 
-    launches_per_step = 9 + 2 + 2 * 2 + 3   # kNN build + 2 queries, 2 classes x (solve + fallback), 3 SpMV
 
-
-def flush_l2(buf):
-    buf.add_(1.0)
-
-
-def time_steps(pipe, precision, steps, stream, flush, sub=None):
-    """CUDA-event time of each step (L2 flushed between steps); optional
-    sub-timing of the weights call."""
+def timed_disk_steps(pipe, precision, steps, stream, flush):
+    """Per-step CUDA-event times (L2 flushed between steps): whole step,
+    weights, and the dominant launch (interior weights)."""
     import torch
-    tot, wts = [], []
+    tot, wts, dom = [], [], []
     for _ in range(steps):
-        flush_l2(flush)
-        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
-        e0.record(stream)
+        flush.add_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
         pipe.knn()
-        e1.record(stream)
-        pipe.weights(precision)
-        e2.record(stream)
+        ev[1].record(stream)
+        pipe.weights_interior(precision)
+        ev[2].record(stream)
+        pipe.weights_boundary(precision)
+        ev[3].record(stream)
         pipe.apply()
-        e3.record(stream)
-        e3.synchronize()
-        tot.append(e0.elapsed_time(e3))
-        wts.append(e1.elapsed_time(e2))
-    return np.array(tot), np.array(wts)
+        ev[4].record(stream)
+        ev[4].synchronize()
+        tot.append(ev[0].elapsed_time(ev[4]))
+        wts.append(ev[1].elapsed_time(ev[3]))
+        dom.append(ev[1].elapsed_time(ev[2]))
+    return np.array(tot), np.array(wts), np.array(dom)
+
+
+def oracle_rows(ns, rp, col, rows, k, m, ops):
+    """Oracle weights of arbitrary CSR rows (local renumbering, rows first);
+    returns {row: [R, n]}."""
+    from oracle import oracle as O
+    sts = [col[rp[i]:rp[i + 1]] for i in rows]
+    others = np.setdiff1d(np.unique(np.concatenate(sts)), rows)
+    order = np.concatenate([rows, others])
+    remap = np.full(ns.N, -1, dtype=np.int64)
+    remap[order] = np.arange(len(order))
+    lcol = np.concatenate([remap[s] for s in sts]).astype(np.int32)
+    lrp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum([len(s) for s in sts], out=lrp[1:])
+    vals, st, _ = O.weights(ns.pts[order], lrp, lcol, k, m, ops, normals=ns.normals[order],
+                            rows=(0, len(rows)), nthreads=O.nthreads_default())
+    return {int(i): vals[:, lrp[t]:lrp[t + 1]] for t, i in enumerate(rows)}
 
 
 def sampled_error(pipe, rows_per_class=200, seed=0):
-    """Max relative weight error (per node and operator) and monomial
-    reproduction residual on sampled rows, against the oracle."""
+    """Max / median relative weight error per operator and the scaled
+    monomial-reproduction residual on sampled rows, against the oracle."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from oracle import oracle as O
     from _helpers import monomial_residual, rel_err_rows
-    ns = pipe.ns
-    rp = pipe.rp_h
+    ns, rp = pipe.ns, pipe.rp_h
     col = pipe.col.cpu().numpy()
     got = {"lap": pipe.op.cpu().numpy(), "dx": pipe.dx.cpu().numpy(),
            "dy": pipe.dy.cpu().numpy(), "dn": pipe.op.cpu().numpy()}
     rng = np.random.default_rng(seed)
     out = {}
-    for (b, e), spec, names in (((pipe.ib, pipe.ie), WORKLOAD["interior"], ["lap", "dx", "dy"]),
-                                ((pipe.bb, pipe.be), WORKLOAD["boundary"], ["dn"])):
+    for (b, e), spec, names in (((pipe.ib, pipe.ie), DISK["interior"], ["lap", "dx", "dy"]),
+                                ((pipe.bb, pipe.be), DISK["boundary"], ["dn"])):
         rows = np.sort(rng.choice(np.arange(b, e), min(rows_per_class, e - b), replace=False))
-        # oracle on a local renumbering: rows first
-        sts = [col[rp[i]:rp[i + 1]] for i in rows]
-        others = np.setdiff1d(np.unique(np.concatenate(sts)), rows)
-        order = np.concatenate([rows, others])
-        remap = np.full(ns.N, -1, dtype=np.int64)
-        remap[order] = np.arange(len(order))
-        lcol = np.concatenate([remap[s] for s in sts]).astype(np.int32)
-        lrp = np.zeros(len(rows) + 1, dtype=np.int64)
-        np.cumsum([len(s) for s in sts], out=lrp[1:])
-        ops = sum({"lap": 1, "dx": 2, "dy": 4, "dn": 16}[nm] for nm in names)
-        vals, st, _ = O.weights(ns.pts[order], lrp, lcol, spec["k"], spec["m"], ops,
-                                normals=ns.normals[order], rows=(0, len(rows)), nthreads=8)
+        ref = oracle_rows(ns, rp, col, rows, spec["k"], spec["m"], spec["ops"])
         for oi, nm in enumerate(names):
             w_ref = np.zeros_like(got[nm])
-            for t, i in enumerate(rows):
-                w_ref[rp[i]:rp[i + 1]] = vals[oi, lrp[t]:lrp[t + 1]]
+            for i in rows:
+                w_ref[rp[i]:rp[i + 1]] = ref[int(i)][oi]
             err = rel_err_rows(got[nm], w_ref, rp, rows)
             mono = monomial_residual(ns.pts, ns.normals, rp, col, got[nm], nm, spec["m"], rows)
             out[nm] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
@@ -242,17 +376,59 @@ def sampled_error(pipe, rows_per_class=200, seed=0):
     return out
 
 
-# ----------------------------------------------------------- CPU baseline
-def cpu_baseline(ns, rp, col_h, seconds=15.0, seed=0):
-    """The oracle timed on the host cores on a bounded sample of the same
-    workload: brute-force kNN for S_k queries and weights for S_w rows, all
-    cores.  Returns nodes/s of kNN + weights per node."""
+def poisson_error(ns, rp, col, op_vals):
+    """Max-norm error of the manufactured Poisson problem on the disk with
+    holes (Section 2.3.2 assembly): interior rows  Laplacian weights, u_xx +
+    u_yy = f; outer circle Dirichlet rows (identity), hole boundaries Neumann
+    rows (d/dn weights), u = sin(pi x) sin(pi y).  Solved with scipy (not
+    timed)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    import nodesets as NS
+    A = sp.csr_matrix((op_vals, col, rp), shape=(ns.N, ns.N)).tolil()
+    u = NS.sin_product(ns.pts)
+    rhs = NS.sin_product_lap(ns.pts)
+    g = NS.sin_product_grad(ns.pts)
+    for i in np.nonzero(ns.dirichlet)[0]:
+        A.rows[i] = [int(i)]
+        A.data[i] = [1.0]
+        rhs[i] = u[i]
+    nb = np.nonzero(ns.neumann)[0]
+    rhs[nb] = (g[nb] * ns.normals[nb]).sum(1)
+    sol = spla.spsolve(A.tocsc(), rhs)
+    return float(np.abs(sol - u).max())
+
+
+def poisson_comparison(P, ctx, device, n_target=100_000):
+    """Poisson error with plain FP64 weights and with the chosen form on a
+    smaller disk (the sparse direct solve of the full size is not needed to
+    compare them): 'equal' means within 1% relative."""
+    import torch
+    ns, rp = make_disk(7, n_target)
+    pipe = DiskPipeline(P, ctx, ns, rp, device)
+    out = {}
+    for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        pipe.knn()
+        pipe.weights_interior(prec)
+        pipe.weights_boundary(prec)
+        torch.cuda.synchronize()
+        out[name] = poisson_error(ns, rp, pipe.col.cpu().numpy(), pipe.op.cpu().numpy())
+    out["N"] = ns.N
+    out["relative_difference"] = abs(out["fp32_ir"] - out["fp64"]) / out["fp64"]
+    out["equal_within_1pct"] = out["relative_difference"] <= 0.01
+    return out
+
+
+def cpu_baseline_disk(ns, rp, col_h, seconds=15.0, seed=0):
+    """The oracle timed on the host cores on a bounded sample of the disk
+    workload: brute-force kNN of S_k queries and weights of S_w rows (interior
+    and boundary in proportion), all cores.  nodes/s of kNN + weights."""
     from oracle import oracle as O
     threads = O.nthreads_default()
     rng = np.random.default_rng(seed)
     (ib, ie), (bb, be) = ns.classes["interior"], ns.classes["boundary"]
     frac_b = (be - bb) / ns.N
-    # kNN: calibrate on a few queries, then size the sample to ~1/3 of the budget
     q = rng.choice(np.arange(ib, ie), 64, replace=False)
     t0 = time.perf_counter()
     O.knn(ns.pts, 25, queries=q, nthreads=threads)
@@ -262,21 +438,13 @@ def cpu_baseline(ns, rp, col_h, seconds=15.0, seed=0):
     t0 = time.perf_counter()
     O.knn(ns.pts, 25, queries=qi, nthreads=threads)
     t_knn = (time.perf_counter() - t0) / sk
-    # weights: interior rows and boundary rows in their proportion
     sw = 20000
     t_w = 0.0
-    for (b, e), n, ops, share in (((ib, ie), 25, 1 | 2 | 4, 1 - frac_b), ((bb, be), 30, 16, frac_b)):
+    for (b, e), spec, share in (((ib, ie), DISK["interior"], 1 - frac_b),
+                                ((bb, be), DISK["boundary"], frac_b)):
         rows = np.sort(rng.choice(np.arange(b, e), max(1, int(sw * share)), replace=False))
-        sts = [col_h[rp[i]:rp[i + 1]] for i in rows]
-        others = np.setdiff1d(np.unique(np.concatenate(sts)), rows)
-        order = np.concatenate([rows, others])
-        remap = np.full(ns.N, -1, dtype=np.int64)
-        remap[order] = np.arange(len(order))
-        lcol = np.concatenate([remap[s] for s in sts]).astype(np.int32)
-        lrp = np.arange(len(rows) + 1, dtype=np.int64) * n
         t0 = time.perf_counter()
-        O.weights(ns.pts[order], lrp, lcol, 5, 4, ops, normals=ns.normals[order],
-                  rows=(0, len(rows)), nthreads=threads)
+        oracle_rows(ns, rp, col_h, rows, spec["k"], spec["m"], spec["ops"])
         t_w += (time.perf_counter() - t0) / len(rows) * share
     return {"value": 1.0 / (t_knn + t_w), "unit": "nodes/s", "cores": threads, "kind": "oracle",
             "sample": f"{sk} brute-force kNN queries over all {ns.N} nodes + {sw} weight rows "
@@ -284,20 +452,383 @@ def cpu_baseline(ns, rp, col_h, seconds=15.0, seed=0):
             "knn_s_per_node": t_knn, "weights_s_per_node": t_w}
 
 
+def run_disk(args, rk):
+    import torch
+    import paper_1912_13282_gb300 as P
+    device = rk.local
+    stream = torch.cuda.current_stream(device)
+    ctx = P.Context(device, stream)
+    n_target = args.n_target or DISK["N_target"]
+    ns, rp = make_disk(rk.rank, n_target)
+    pipe = DiskPipeline(P, ctx, ns, rp, device)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=f"cuda:{device}")
+    fp64_peak = ctx.measure_fma_peak(0)
+    fp32_peak = ctx.measure_fma_peak(1)
+    for _ in range(max(3, args.warmup)):
+        pipe.step(P.FP64)
+        pipe.step(P.FP32_IR)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    rk.barrier()
+    torch.cuda.synchronize()
+    t64, w64, d64 = timed_disk_steps(pipe, P.FP64, args.steps, stream, flush)
+    rk.barrier()
+    torch.cuda.synchronize()
+    tot, wts, dom = timed_disk_steps(pipe, P.FP32_IR, args.steps, stream, flush)
+    torch.cuda.synchronize()
+    rk.barrier()
+    clk = clocks.stop()
+    ms, ms64 = rk.max([tot.sum(), t64.sum()])
+    status = pipe.status.cpu().numpy()
+    fallback = float((status == P.binding.ST_FALLBACK).mean())
+    (n_all,) = rk.sum([ns.N])
+    value = throughput(n_all, ms, args.steps)
+
+    e2e = None
+    if not args.no_e2e:
+        h_pts = torch.from_numpy(ns.pts).pin_memory()
+        h_nrm = torch.from_numpy(ns.normals).pin_memory()
+        h_out = [torch.empty(pipe.nnz, dtype=torch.float64).pin_memory() for _ in range(3)]
+        e_ms = []
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pipe.pts.copy_(h_pts, non_blocking=True)
+            pipe.nrm.copy_(h_nrm, non_blocking=True)
+            pipe.step(P.FP32_IR)
+            for h, d in zip(h_out, (pipe.op, pipe.dx, pipe.dy)):
+                h.copy_(d, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        (e_tot,) = rk.max([float(np.sum(e_ms))])
+        e2e = {"value": throughput(n_all, e_tot, args.steps), "unit": "nodes/s",
+               "h2d_bytes_per_step": int((h_pts.numel() + h_nrm.numel()) * 8),
+               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in h_out))}
+
+    wi = DISK["interior"]
+    Ni = pipe.ie - pipe.ib
+    f64 = mixed_fp64_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
+    dom_ms = float(np.mean(dom))
+    achieved = f64 / (dom_ms * 1e-3)
+    traffic = stored_traffic("k_weights_mixed<2,2,3>")
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "traffic": None if traffic is None else traffic["bytes_per_row"] * Ni,
+            "kernel": "k_weights_mixed<2,2,3> (interior rows; FP32 LU + FP64 refinement)",
+            "algorithmic": "FP64 flops per interior stencil: A block, Q, RHS, one full residual, "
+                           "constraint residual, updates (bench.mixed_fp64_flops)",
+            "peak_source": "FP64 FMA peak measured in this run (mm_measure_fma_peak); "
+                           "MEASURED_PEAKS.json has no FP64 figure"}
+    f64_plain = fp64_solve_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
+    line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": rk.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": DISK["workload"], "N": ns.N,
+                       "precision": "fp32 LU + fp64 refinement (fp64 fallback)",
+                       "l2": "256 MiB buffer written between timed steps",
+                       "step": "grid kNN + weights (2 classes) + 3 operator applications"},
+            "fp64_plain": {"value": throughput(n_all, ms64, args.steps), "unit": "nodes/s",
+                           "ms_per_step": ms64 / args.steps, "weights_ms": float(np.mean(w64)),
+                           "dominant_ms": float(np.mean(d64)),
+                           "roofline_frac": f64_plain / (float(np.mean(d64)) * 1e-3) / fp64_peak},
+            "speedup_vs_fp64_plain": ms64 / ms, "weights_ms": float(np.mean(wts)),
+            "fallback_fraction": fallback, "roofline": roof,
+            "peaks_measured": {"fp64_flops": fp64_peak, "fp32_flops": fp32_peak},
+            "e2e": e2e, "clocks": clk, "gpu_launches": DISK_LAUNCHES_PER_STEP * args.steps}
+    if rk.rank == 0 and not args.no_error:
+        line["error"] = sampled_error(pipe)
+    if rk.rank == 0 and not args.no_poisson:
+        line["poisson"] = poisson_comparison(P, ctx, device)
+    if rk.rank == 0 and rk.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_disk(ns, rp, pipe.col.cpu().numpy())
+    ctx.close()
+    return line
+
+
+# ------------------------------------------------------------ ball workload
+BALL = {"workload": "unit ball, 4e6 nodes: interior n=35 r^3 deg 2, refined |x|<0.5 n=60 r^3 deg 3, "
+                    "boundary n=45 d/dn; one persistent launch, autotuned tiles",
+        "N_target": 4_000_000,
+        "classes": [("interior", 35, 3, 2, 1 | 2 | 4 | 8), ("refined", 60, 3, 3, 1 | 2 | 4 | 8),
+                    ("boundary", 45, 3, 2, 16)]}
+
+
+def run_ball(args, rk):
+    import torch
+
+    import nodesets as NS
+    import paper_1912_13282_gb300 as P
+    device = rk.local
+    stream = torch.cuda.current_stream(device)
+    ctx = P.Context(device, stream)
+    ns = NS.ball(args.n_target or BALL["N_target"], seed=rk.rank)
+    sizes = np.zeros(ns.N, dtype=np.int64)
+    for cname, n, *_ in BALL["classes"]:
+        b, e = ns.classes[cname]
+        sizes[b:e] = n
+    rp = np.zeros(ns.N + 1, dtype=np.int64)
+    np.cumsum(sizes, out=rp[1:])
+    dv = f"cuda:{device}"
+    pts, nrm = torch.from_numpy(ns.pts).to(dv), torch.from_numpy(ns.normals).to(dv)
+    rp_d = torch.from_numpy(rp).to(dv)
+    nnz = int(rp[-1])
+    col = torch.empty(nnz, dtype=torch.int32, device=dv)
+    vals = [torch.zeros(nnz, dtype=torch.float64, device=dv) for _ in range(4)]   # lap/dn, dx, dy, dz
+    status = torch.empty(ns.N, dtype=torch.int32, device=dv)
+    ranges = []
+    classes = []
+    for cname, n, k, m, ops in BALL["classes"]:
+        b, e = ns.classes[cname]
+        ranges.append((b, e, n, col[int(rp[b]):int(rp[e])]))
+        vv = vals if ops != 16 else [vals[0]]
+        classes.append(P.Context.weights_class(ops, k, m, pts, rp_d, col, vv, row_begin=b,
+                                               row_end=e, n_max=n, normals=nrm, status=status))
+    u = torch.from_numpy(NS.sin_product(ns.pts)).to(dv)
+    y = torch.empty_like(u)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dv)
+
+    def step(prec):
+        ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
+        ctx.rbffd_weights_batched(classes, precision=prec)
+        for v in vals:
+            ctx.apply_operator(rp_d, col, v, u, y)
+
+    ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
+    tuned = {}
+    for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        cfg, t = ctx.autotune_batched(classes, precision=prec, sample_rows=32768)
+        tuned[name] = {"warps_per_block": cfg[0], "blocks_per_sm": cfg[1], "chunk_rows": cfg[2],
+                       "sample_ms": t}
+    for _ in range(max(3, args.warmup)):
+        step(P.FP64)
+        step(P.FP32_IR)
+    torch.cuda.synchronize()
+    res = {}
+    clocks = ClockSampler(device)
+    clocks.start()
+    for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        rk.barrier()
+        tt, ww = [], []
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
+            ev[1].record(stream)
+            ctx.rbffd_weights_batched(classes, precision=prec)
+            ev[2].record(stream)
+            for v in vals:
+                ctx.apply_operator(rp_d, col, v, u, y)
+            ev[3].record(stream)
+            ev[3].synchronize()
+            tt.append(ev[0].elapsed_time(ev[3]))
+            ww.append(ev[1].elapsed_time(ev[2]))
+        (ms,) = rk.max([float(np.sum(tt))])
+        (n_all,) = rk.sum([ns.N])
+        res[name] = {"ms_per_step": ms / args.steps, "weights_ms": float(np.mean(ww)),
+                     "value": throughput(n_all, ms, args.steps)}
+    clk = clocks.stop()
+    st = status.cpu().numpy()
+    line = {"metric": METRIC, "value": res["fp32_ir"]["value"], "unit": "nodes/s",
+            "n_gpus": rk.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["fp32_ir"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": BALL["workload"], "N": ns.N,
+                       "classes": {c: ns.classes[c] for c, *_ in BALL["classes"]}},
+            "fp64_plain": res["fp64"], "fp32_ir": res["fp32_ir"],
+            "speedup_vs_fp64_plain": res["fp64"]["ms_per_step"] / res["fp32_ir"]["ms_per_step"],
+            "fallback_fraction": float((st == P.binding.ST_FALLBACK).mean()),
+            "autotuned": tuned, "clocks": clk,
+            "gpu_launches": (11 + 2 + 4) * args.steps}
+    ctx.close()
+    return line
+
+
+# ----------------------------------------------------------- batch workload
+def run_batch(args, rk):
+    import torch
+
+    import nodesets as NS
+    import paper_1912_13282_gb300 as P
+    device = rk.local
+    dv = f"cuda:{device}"
+    ctx = P.Context(device, torch.cuda.current_stream(device))
+    scale = (args.n_target / 2.4e7) if args.n_target else 1.0
+    specs = NS.batch_geometries(64, seed=rk.rank, scale=scale)
+    params = {2: [(12, 3, 2), (25, 5, 4)], 3: [(35, 3, 2), (60, 3, 3)]}
+    geoms = []
+    t0 = time.time()
+    for sp in specs:
+        ns = NS.make_geometry(sp)
+        n, k, m = params[sp["dim"]][sp["stencil_choice"]]
+        rp = np.arange(ns.N + 1, dtype=np.int64) * n
+        g = {"ns": ns, "n": n, "k": k, "m": m, "pts": torch.from_numpy(ns.pts).to(dv),
+             "rp": torch.from_numpy(rp).to(dv), "col": torch.empty(ns.N * n, dtype=torch.int32, device=dv),
+             "lap": torch.zeros(ns.N * n, dtype=torch.float64, device=dv),
+             "fixed": torch.from_numpy(ns.normals.any(axis=1).astype(np.uint8)).to(dv),
+             "u0": torch.from_numpy(NS.sin_product(ns.pts)).to(dv),
+             "dt": 0.1 * ns.h ** 2}
+        g["u"] = g["u0"].clone()
+        g["work"] = torch.empty_like(g["u"])
+        ctx.knn_stencils(g["pts"], [(0, ns.N, n, g["col"])], method=P.KNN_GRID)
+        geoms.append(g)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    N = sum(g["ns"].N for g in geoms)
+    classes = [P.Context.weights_class(1, g["k"], g["m"], g["pts"], g["rp"], g["col"], [g["lap"]],
+                                       n_max=g["n"]) for g in geoms]
+    res = {}
+    for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        ctx.autotune_batched(classes, precision=prec, sample_rows=8192)
+
+        def run():
+            ctx.rbffd_weights_batched(classes, precision=prec)
+            for g in geoms:
+                ctx.diffuse(g["rp"], g["col"], g["lap"], g["fixed"], g["dt"], 100, g["u"], g["work"])
+
+        for g in geoms:
+            g["u"].copy_(g["u0"])
+        run()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device)
+        side.wait_stream(torch.cuda.current_stream(device))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                ctx.set_stream(side)
+                run()
+        ctx.set_stream(torch.cuda.current_stream(device))
+        torch.cuda.synchronize()
+        for _ in range(max(1, args.warmup)):
+            graph.replay()
+        torch.cuda.synchronize()
+        rk.barrier()
+        times = []
+        stream = torch.cuda.current_stream(device)
+        for _ in range(args.steps):
+            for g in geoms:
+                g["u"].copy_(g["u0"])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        (ms,) = rk.max([float(np.sum(times))])
+        (n_all,) = rk.sum([N])
+        res[name] = {"ms_per_step": ms / args.steps, "value": throughput(n_all, ms, args.steps)}
+        del graph
+    line = {"metric": METRIC, "value": res["fp32_ir"]["value"], "unit": "nodes/s",
+            "n_gpus": rk.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["fp32_ir"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "64 2D/3D node sets, log-uniform 1e4..2e6 nodes, n in {12,25,35,60}: "
+                                   "all Laplacian weights (one persistent launch) + 100 explicit "
+                                   "diffusion steps each, one CUDA graph", "N_total": N,
+                       "node_generation_s": gen_s},
+            "fp64_plain": res["fp64"], "fp32_ir": res["fp32_ir"],
+            "speedup_vs_fp64_plain": res["fp64"]["ms_per_step"] / res["fp32_ir"]["ms_per_step"]}
+    ctx.close()
+    return line
+
+
+# ------------------------------------------------------- surrogate workload
+def run_surrogate(args, rk):
+    import torch
+
+    import paper_1912_13282_gb300 as P
+    from paper_1912_13282_gb300 import surrogate as S
+    device = rk.local
+    ctx = P.Context(device, torch.cuda.current_stream(device))
+    n, k, m = 25, 5, 4
+    ntrain = 1 << 20
+    neval = args.n_target or 1_000_000
+    t0 = time.time()
+    data = S.make_dataset(ctx, ntrain, seed=1 + 1000 * rk.rank)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    net = P.MLP(ctx, 2 * n, n, seed=rk.rank)
+    t0 = time.time()
+    losses = S.train(net, data["x"], data["t"], epochs=20, batch=4096, lr=3e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del data
+    pts, rp, col = S.make_stencils(ctx, neval, seed=10 ** 6 + rk.rank)
+    vals = {nm: torch.zeros(neval * n, dtype=torch.float64, device="cuda") for nm in ("fp64", "ir", "sur")}
+    status = torch.empty(neval, dtype=torch.int32, device="cuda")
+    rho = torch.empty(neval, dtype=torch.float32, device="cuda")
+    tau = 1e-3
+    stream = torch.cuda.current_stream(device)
+
+    def run(name):
+        if name == "sur":
+            P.rbffd_weights_surrogate(ctx, net, k, m, pts, rp, col, 0, neval, n, tau, vals["sur"],
+                                      status, rho)
+        else:
+            ctx.rbffd_weights(P.LAP, k, m, pts, rp, col, [vals[name]], row_end=neval, n_max=n,
+                              precision=P.FP64 if name == "fp64" else P.FP32_IR)
+
+    res = {}
+    for name in ("fp64", "ir", "sur"):
+        for _ in range(max(1, args.warmup)):
+            run(name)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run(name)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        (ms,) = rk.max([float(np.sum(ts))])
+        (n_all,) = rk.sum([neval])
+        res[name] = {"ms": ms / args.steps, "value": throughput(n_all, ms, args.steps)}
+    st = status.cpu().numpy()
+    acc = st == P.binding.ST_ACCEPTED
+    w = vals["sur"].view(neval, n).cpu().numpy()
+    r = vals["fp64"].view(neval, n).cpu().numpy()
+    err = np.abs(w - r).max(1) / np.abs(r).max(1)
+    line = {"metric": METRIC, "value": res["sur"]["value"], "unit": "nodes/s", "n_gpus": rk.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["sur"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32+f64", "data": "synthetic",
+            "config": {"workload": f"surrogate: MLP 50-256x3-25 trained on {ntrain} jittered-patch "
+                                   f"stencils, {neval} held-out stencils (n=25, r^5, deg 4)",
+                       "tau": tau},
+            "fp64_plain": res["fp64"], "fp32_ir": res["ir"], "surrogate": res["sur"],
+            "speedup_vs_fp64_plain": res["fp64"]["ms"] / res["sur"]["ms"],
+            "accept_fraction": float(acc.mean()),
+            "error_vs_fp64": {"accepted_median": float(np.median(err[acc])) if acc.any() else None,
+                              "accepted_p99": float(np.quantile(err[acc], 0.99)) if acc.any() else None,
+                              "fallback_max": float(err[~acc].max()) if (~acc).any() else None},
+            "training": {"samples": ntrain, "steps": int(len(losses)), "seconds": t_train,
+                         "data_seconds": t_data, "loss_first": float(losses[:20].mean()),
+                         "loss_last": float(losses[-50:].mean())}}
+    ctx.close()
+    return line
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
-    rank, world, _ = dist_info()
-    if rank != 0:
+    """The CPU oracle as the reference arm: each step a bounded sample of
+    the disk workload (exhaustive kNN + FP64 weights of 256 interior nodes)
+    on all host cores; rank 0 only."""
+    rk_rank = int(os.environ.get("RANK", "0"))
+    if rk_rank != 0:
         return 0
-    ns, rp = make_workload(0, args.n_target)
-    # stencils for the weight sample come from the oracle itself (exhaustive kNN)
     from oracle import oracle as O
+    ns, rp = make_disk(0, args.n_target or DISK["N_target"])
     threads = O.nthreads_default()
     rng = np.random.default_rng(1)
     vals = []
+    (ib, ie) = ns.classes["interior"]
     for _ in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        (ib, ie), (bb, be) = ns.classes["interior"], ns.classes["boundary"]
         qi = np.sort(rng.choice(np.arange(ib, ie), 256, replace=False))
         idx, _ = O.knn(ns.pts, 25, queries=qi, nthreads=threads)
         order = np.concatenate([qi, np.setdiff1d(np.unique(idx), qi)])
@@ -312,8 +843,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 256 / v * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD["workload"], "sample_per_step": "256 interior nodes: "
-                       "exhaustive kNN + FP64 weights (lap, dx, dy)"},
+            "config": {"workload": DISK["workload"],
+                       "sample_per_step": "256 interior nodes: exhaustive kNN + FP64 weights (lap, dx, dy)"},
             "cpu_baseline": {"value": v, "unit": "nodes/s", "cores": threads, "kind": "oracle",
                              "sample": "256 interior nodes per step"},
             "e2e": {"value": v, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -322,124 +853,22 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- main
-def main():
-    args = parse()
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
     import torch
-    rank, world, local = dist_info()
-    device = local
-    torch.cuda.set_device(device)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{device}"))
+    rk = Ranks("nccl")
+    torch.cuda.set_device(rk.local)
     from paper_1912_13282_gb300 import _build
-    if rank == 0 or world == 1:
+    if rk.local == 0:
         _build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    import paper_1912_13282_gb300 as P
-    stream = torch.cuda.current_stream(device)
-    ctx = P.Context(device, stream)
-    ns, rp = make_workload(rank, args.n_target)
-    pipe = Pipeline(P, ctx, ns, rp, device)
-    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=f"cuda:{device}")
-    peaks = {"fp64_flops": ctx.measure_fma_peak(0), "fp32_flops": ctx.measure_fma_peak(1)}
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    # warm-up (also grows the library workspace before timing)
-    for _ in range(max(3, args.warmup)):
-        pipe.step(P.FP64)
-        pipe.step(P.FP32_IR)
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(device)
-    clocks.start()
-    barrier()
-    tot64, w64 = time_steps(pipe, P.FP64, args.steps, stream, flush)
-    barrier()
-    tot, wts = time_steps(pipe, P.FP32_IR, args.steps, stream, flush)
-    barrier()
-    clk = clocks.stop()
-    ms = float(tot.sum())
-    if world > 1:
-        t = torch.tensor([ms, float(tot64.sum())], device=f"cuda:{device}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms64 = float(t[0]), float(t[1])
-    else:
-        ms64 = float(tot64.sum())
-    status = pipe.status.cpu().numpy()
-    fallback = float((status == P.binding.ST_FALLBACK).mean())
-    value = world * ns.N * args.steps / (ms * 1e-3)
-
-    # end to end: host (pinned) inputs in, weights out, inside the timed region
-    e2e = None
-    if not args.no_e2e:
-        h_pts = torch.from_numpy(ns.pts).pin_memory()
-        h_nrm = torch.from_numpy(ns.normals).pin_memory()
-        h_out = [torch.empty(pipe.nnz, dtype=torch.float64).pin_memory() for _ in range(3)]
-        e_ms = []
-        for it in range(args.steps):
-            flush_l2(flush)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pipe.pts.copy_(h_pts, non_blocking=True)
-            pipe.nrm.copy_(h_nrm, non_blocking=True)
-            pipe.step(P.FP32_IR)
-            for h, d in zip(h_out, (pipe.op, pipe.dx, pipe.dy)):
-                h.copy_(d, non_blocking=True)
-            b.record(stream)
-            b.synchronize()
-            e_ms.append(a.elapsed_time(b))
-        e2e = {"value": world * ns.N / (float(np.mean(e_ms)) * 1e-3), "unit": "nodes/s",
-               "h2d_bytes_per_step": int(h_pts.numel() * 8 + h_nrm.numel() * 8),
-               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in h_out))}
-
-    # roofline of the dominant kernel (the refined-FP32 weights solve)
-    M_i = 25 + 15
-    M_b = 30 + 15
-    Ni, Nb = pipe.ie - pipe.ib, pipe.be - pipe.bb
-    # algorithmic FP64 work of the mixed path: one full residual and one
-    # constraint-row residual per stencil (2 flop per multiply-add)
-    f64 = Ni * (2 * 3 * (25 * M_i + 15 * 25) + 2 * 3 * 25 * 15) + \
-        Nb * (2 * 1 * (30 * M_b + 15 * 30) + 2 * 1 * 30 * 15)
-    w_ms = float(np.mean(wts))
-    achieved = f64 / (w_ms * 1e-3)
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peaks["fp64_flops"] / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / peaks["fp64_flops"], "traffic": None,
-            "kernel": "k_weights_mixed (FP64 residual flops)",
-            "peak_source": "measured FP64 FMA loop on this GPU (mm_measure_fma_peak)"}
-
-    err = None
-    if not args.no_error and rank == 0:
-        err = sampled_error(pipe)
-    cpu = None
-    if not args.no_cpu_baseline and rank == 0 and world == 1:
-        cpu = cpu_baseline(ns, rp, pipe.col.cpu().numpy())
-
-    line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD["workload"], "N": ns.N, "precision": "fp32 LU + fp64 IR",
-                       "l2": "256 MiB buffer written between timed steps",
-                       "step": "grid kNN + weights (2 classes) + 3 operator applications"},
-            "fp64_plain": {"value": world * ns.N * args.steps / (ms64 * 1e-3), "unit": "nodes/s",
-                           "ms_per_step": ms64 / args.steps,
-                           "weights_ms": float(np.mean(w64))},
-            "speedup_vs_fp64_plain": ms64 / ms,
-            "weights_ms": w_ms, "fallback_fraction": fallback,
-            "error": err, "roofline": roof, "peaks_measured": peaks, "cpu_baseline": cpu,
-            "e2e": e2e, "clocks": clk, "gpu_launches": Pipeline.launches_per_step * args.steps}
-    if rank == 0:
+    rk.barrier()
+    run = {"disk": run_disk, "ball": run_ball, "batch": run_batch, "surrogate": run_surrogate}[args.workload]
+    line = run(args, rk)
+    if rk.rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    rk.close()
     return 0
 
 
