@@ -334,7 +334,7 @@ int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
  * weights w~; exact FP64 least-norm projection onto the monomial rows of
  * eq. rbf-system-aug, (Q^T Q) z = l_q - Q^T w~, w = w~ + Q z (FP32 Cholesky of
  * the Jacobi-scaled Gram matrix, FP64 constraint residuals until they hold to
- * 1e-15 relative); judged by the other rows: rho = ||r - Q lambda||_inf /
+ * 1e-15 relative); checked against the other rows: rho = ||r - Q lambda||_inf /
  * ||l_phi||_inf with r = l_phi - A w and lambda the least-squares multipliers
  * (FP32).  rho <= tau: weights w / s^2 stored, status MM_ST_ACCEPTED;
  * otherwise the FP64 solve (status MM_ST_FALLBACK).  2D only, n == n_out of

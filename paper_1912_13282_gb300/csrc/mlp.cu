@@ -4,7 +4,7 @@
 // the tensor cores (mma.sync m16n8k16), trained on weights the method itself
 // produces.  Its predictions are projected in FP64 onto the monomial rows
 // Q^T w = l_q of the augmented system (Section 2.2.2, eq. rbf-system-aug), then
-// judged by the remaining rows' residual; rejected stencils get the FP64 solve.
+// checked against the remaining rows' residual; rejected stencils get the FP64 solve.
 //
 // Layout: feature width padded to 64, outputs to 32 (zero weights and inputs in
 // the padding), hidden width 256, 3 hidden layers.  Parameters are FP32
@@ -390,13 +390,13 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
     }
 }
 
-// ------------------------------------------------- projection and judge
+// ------------------------------------------------- projection and residual check
 // One warp per stencil (n <= 32, l <= 32).  wt: predicted scaled Laplacian
 // weights [n] (FP32).  Least-norm correction onto Q^T w = l_q:
 //     w = wt + Q z,  (Q^T Q) z = l_q - Q^T wt,
 // solved with an FP32 Cholesky of the Jacobi-scaled Gram matrix and FP64
 // constraint residuals (up to 4 passes, until the rows hold to 1e-15 relative).
-// Judge: r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least squares),
+// Residual check: r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least squares),
 // rho = ||r - Q lambda||_inf / ||l_phi||_inf; accept if rho <= tau (FP32).
 struct ProjParams {
     WParams P;              // LAP only, k, m, row range, output vals[0]
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             }
             __syncwarp();
         }
-        // judge (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r, e = r - Q lambda
+        // residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r, e = r - Q lambda
         if (lane < n) s_w32[wib][lane] = (float)s_w[wib][lane];
         __syncwarp();
         float lphi = 0.f;
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
     }
 }
 
-// the FP64 solver for stencils the judge rejected
+// the FP64 solver for stencils the residual check rejected
 template <int DIM>
 __global__ void __launch_bounds__(128) k_surrogate_fallback(WParams P) {
     extern __shared__ double smem[];

@@ -1,6 +1,6 @@
 """The BF16 surrogate network against the FP64 CPU oracle (forward and
 gradients), its training, checkpointing, and the surrogate weights path
-(projection, judge, FP64 fallback)."""
+(projection, residual check, FP64 fallback)."""
 import numpy as np
 import pytest
 import torch
@@ -125,7 +125,7 @@ def test_training_reduces_loss(trained):
 def test_surrogate_weights_path(P, ctx, oracle, trained):
     """Held-out stencils: accepted rows reproduce the monomials to 1e-12 and
     equal the oracle's FP64 projection of the same prediction; rejected rows
-    equal the FP64 solve; the judge's rho agrees with the oracle's."""
+    equal the FP64 solve; the residual check's rho agrees with the oracle's."""
     from paper_1912_13282_gb300 import surrogate as S
     net, _ = trained
     count = 4096
