@@ -8,11 +8,20 @@
 // cannot finish to a second launch, the FP64 solver, through a queue of
 // (class, row) pairs.
 //
+// Classes need different amounts of shared memory per stencil.  A CTA gets
+// room for W stencils of the smallest class (at least one of the largest);
+// classes are grouped into phases by how many stencils of them fit at once,
+// and in each phase only that many warps of the CTA take work (from the
+// phase's own counter), each with a slot of the CTA's memory divided by that
+// number.  CTAs move from phase to phase on their own (a CTA barrier between
+// phases, no inter-CTA waiting).
+//
 // The autotuner times launch shapes on a sample of each class and keeps the
 // fastest per batch signature in the context (saved/loaded as a text table).
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -27,16 +36,20 @@ constexpr int kMaxBatchClasses = 96;
 typedef unsigned long long u64;
 
 struct BatchParams {
-    WParams cls[kMaxBatchClasses];
+    WParams cls[kMaxBatchClasses];          // in phase order
     int64_t prefix[kMaxBatchClasses + 1];   // first work item of each class
     signed char variant[kMaxBatchClasses];  // mixed-kernel shape per class
     int nclasses;
+    int nphases;
+    int phase_end[kMaxBatchClasses];        // one past the last class of each phase
+    int phase_warps[kMaxBatchClasses];      // warps of a CTA working in the phase
+    int phase_slot[kMaxBatchClasses];       // shared-memory bytes per working warp
     int chunk_rows;
     int64_t total_items;
-    int *queue;                             // work counter
+    int *queue;                             // [nphases] work counters
     u64 *fb_list;                           // (class << 32) | row
     int *fb_count;
-    size_t warp_bytes;
+    int fb_slot;                            // FP64 slot bytes of the fallback launch
 };
 
 static_assert(sizeof(BatchParams) <= 32000, "batched kernel parameters exceed the 32 KB limit");
@@ -64,8 +77,8 @@ __device__ bool mixed_dispatch_d(int v, const WParams &P, int64_t row, char *bas
     return mixed_dispatch_r<DIM, 3>(rsel, P, row, base);
 }
 
-__device__ int class_of(const BatchParams &B, int64_t item) {
-    int lo = 0, hi = B.nclasses - 1;
+__device__ int class_of(const BatchParams &B, int64_t item, int cb, int ce) {
+    int lo = cb, hi = ce - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (B.prefix[mid] <= item) lo = mid;
@@ -78,38 +91,47 @@ template <bool MIXED>
 __global__ void __launch_bounds__(256) k_weights_batched(const __grid_constant__ BatchParams B) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    char *base = (char *)smem + (size_t)wib * B.warp_bytes;
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(B.queue, 1);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= B.total_items) break;          // every item is taken once
-        const int c = class_of(B, item);
-        const WParams &P = B.cls[c];
-        const int64_t r0 = P.row_begin + (item - B.prefix[c]) * (int64_t)B.chunk_rows;
-        const int64_t r1 = min(r0 + (int64_t)B.chunk_rows, P.row_end);
-        const int v = B.variant[c];
-        for (int64_t row = r0; row < r1; ++row) {
-            if (MIXED) {
-                const bool q = P.dim == 2 ? mixed_dispatch_d<2>(v, P, row, base)
-                                          : mixed_dispatch_d<3>(v, P, row, base);
-                if (q && lane == 0) {
-                    const int slot = atomicAdd(B.fb_count, 1);
-                    B.fb_list[slot] = ((u64)c << 32) | (u64)row;
+    int cb = 0;
+    for (int p = 0; p < B.nphases; ++p) {
+        const int ce = B.phase_end[p];
+        if (wib < B.phase_warps[p]) {
+            char *base = (char *)smem + (size_t)wib * B.phase_slot[p];
+            const int64_t ib = B.prefix[cb], ie = B.prefix[ce];
+            for (;;) {
+                long long item = 0;
+                if (lane == 0) item = ib + atomicAdd(&B.queue[p], 1);
+                item = __shfl_sync(kFull, item, 0);
+                if (item >= ie) break;            // every item of the phase is taken once
+                const int c = class_of(B, item, cb, ce);
+                const WParams &P = B.cls[c];
+                const int64_t r0 = P.row_begin + (item - B.prefix[c]) * (int64_t)B.chunk_rows;
+                const int64_t r1 = min(r0 + (int64_t)B.chunk_rows, P.row_end);
+                const int v = B.variant[c];
+                for (int64_t row = r0; row < r1; ++row) {
+                    if (MIXED) {
+                        const bool q = P.dim == 2 ? mixed_dispatch_d<2>(v, P, row, base)
+                                                  : mixed_dispatch_d<3>(v, P, row, base);
+                        if (q && lane == 0) {
+                            const int slot = atomicAdd(B.fb_count, 1);
+                            B.fb_list[slot] = ((u64)c << 32) | (u64)row;
+                        }
+                        __syncwarp();
+                    } else {
+                        if (P.dim == 2) fp64_row<2>(P, row, (double *)base, false);
+                        else fp64_row<3>(P, row, (double *)base, false);
+                    }
                 }
-                __syncwarp();
-            } else {
-                if (P.dim == 2) fp64_row<2>(P, row, (double *)base, false);
-                else fp64_row<3>(P, row, (double *)base, false);
             }
         }
+        __syncthreads();
+        cb = ce;
     }
 }
 
 __global__ void __launch_bounds__(256) k_weights_batched_fallback(const __grid_constant__ BatchParams B) {
     extern __shared__ double smem[];
     const int wib = threadIdx.x >> 5;
-    double *base = (double *)((char *)smem + (size_t)wib * B.warp_bytes);
+    double *base = (double *)((char *)smem + (size_t)wib * B.fb_slot);
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t count = *B.fb_count;
@@ -125,7 +147,9 @@ __global__ void __launch_bounds__(256) k_weights_batched_fallback(const __grid_c
 
 // ------------------------------------------------------------------ host
 struct Prepared {
-    BatchParams *B = nullptr;        // host copy (large: heap)
+    std::vector<WParams> cls;        // classes of the persistent launch (call order)
+    std::vector<size_t> foot;        // shared-memory bytes per stencil of each
+    size_t fb_slot = 0;              // FP64 bytes per stencil, largest class
     std::vector<int> separate;       // classes launched on their own
     int64_t rows = 0;
     bool mixed = false;
@@ -142,22 +166,22 @@ std::string signature_of(const std::vector<WParams> &cls, int precision) {
     return s;
 }
 
-mm_launch_config default_config(mm_ctx *ctx, size_t warp_bytes) {
+mm_launch_config default_config() {
     mm_launch_config c;
     c.warps_per_block = 4;
-    while (c.warps_per_block > 1 && warp_bytes * c.warps_per_block > 96 * 1024) c.warps_per_block /= 2;
-    c.blocks_per_sm = 0;   // filled from the occupancy calculator
+    c.blocks_per_sm = 0;   // from the occupancy calculator
     c.chunk_rows = 16;
-    (void)ctx;
     return c;
 }
 
-// Builds the kernel parameter block; classes the persistent kernel cannot
-// take (mixed precision with 5 operators) are listed in `separate`.
+size_t round16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Validates the classes and computes their footprints; classes the
+// persistent kernel cannot take (mixed precision with 5 operators) are
+// listed in `separate`.
 int prepare(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int precision,
             int64_t row_cap, Prepared &out, std::vector<WeightsJob> &jobs) {
     out.mixed = precision == MM_FP32_IR;
-    std::vector<WParams> cls;
     jobs.clear();
     for (int i = 0; i < nclasses; ++i) {
         const mm_weights_class &C = classes[i];
@@ -173,26 +197,58 @@ int prepare(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int prec
             out.separate.push_back(i);
             continue;
         }
-        cls.push_back(P);
-    }
-    out.signature = signature_of(cls, precision);
-    BatchParams *B = new BatchParams();
-    memset(B, 0, sizeof(BatchParams));
-    B->nclasses = (int)cls.size();
-    size_t wb = 0;
-    for (size_t i = 0; i < cls.size(); ++i) {
-        B->cls[i] = cls[i];
-        const WParams &P = cls[i];
-        wb = std::max(wb, fp64_warp_doubles(P.M_max, P.pitch64, P.n_max, P.dim) * sizeof(double));
-        if (out.mixed) {
-            const int rpl = (P.M_max + 31) / 32;
-            wb = std::max(wb, mixed_layout(P.n_max, P.l, mixed_cols(P.R), P.dim).bytes);
-            B->variant[i] = (signed char)mixed_variant(P.dim, rpl, P.R);
-        }
+        const size_t f64 = round16(fp64_warp_doubles(P.M_max, P.pitch64, P.n_max, P.dim) * sizeof(double));
+        const size_t fm = out.mixed ? round16(mixed_layout(P.n_max, P.l, mixed_cols(P.R), P.dim).bytes) : f64;
+        out.cls.push_back(P);
+        out.foot.push_back(fm);
+        out.fb_slot = std::max(out.fb_slot, f64);
         out.rows += P.row_end - P.row_begin;
     }
-    B->warp_bytes = (wb + 15) & ~size_t(15);
-    out.B = B;
+    out.signature = signature_of(out.cls, precision);
+    return MM_OK;
+}
+
+// Phase plan for W warps per CTA: shared memory S = max(W * smallest
+// footprint, largest footprint) (capped by the device), classes ordered by the
+// number of stencils that fit in S at once, descending.
+int build_params(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg, BatchParams &B,
+                 size_t &smem) {
+    const int W = cfg.warps_per_block;
+    const int nc = (int)pr.cls.size();
+    size_t fmin = ~size_t(0), fmax = 0;
+    for (size_t f : pr.foot) { fmin = std::min(fmin, f); fmax = std::max(fmax, f); }
+    if (fmax > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: %zu bytes of shared memory per stencil", fmax);
+    smem = std::min(std::max((size_t)W * fmin, fmax), (size_t)ctx->smem_optin);
+    std::vector<int> order(nc), fit(nc);
+    for (int i = 0; i < nc; ++i) {
+        order[i] = i;
+        fit[i] = (int)std::min<size_t>(W, smem / pr.foot[i]);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fit[a] > fit[b]; });
+    memset(&B, 0, sizeof(BatchParams));
+    B.nclasses = nc;
+    B.nphases = 0;
+    B.chunk_rows = cfg.chunk_rows;
+    int64_t items = 0;
+    for (int j = 0; j < nc; ++j) {
+        const int i = order[j];
+        const WParams &P = pr.cls[i];
+        B.cls[j] = P;
+        if (pr.mixed) B.variant[j] = (signed char)mixed_variant(P.dim, (P.M_max + 31) / 32, P.R);
+        B.prefix[j] = items;
+        items += (P.row_end - P.row_begin + cfg.chunk_rows - 1) / cfg.chunk_rows;
+        const bool new_phase = B.nphases == 0 || B.phase_warps[B.nphases - 1] != fit[i];
+        if (new_phase) {
+            B.phase_warps[B.nphases] = fit[i];
+            B.phase_slot[B.nphases] = (int)(smem / fit[i] & ~size_t(15));
+            ++B.nphases;
+        }
+        B.phase_end[B.nphases - 1] = j + 1;
+    }
+    B.prefix[nc] = items;
+    B.total_items = items;
+    B.fb_slot = (int)pr.fb_slot;
+    if (items >= (int64_t(1) << 31)) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: too many work items");
     return MM_OK;
 }
 
@@ -210,53 +266,50 @@ cudaError_t occupancy(const mm_ctx *ctx, const void *kern, int threads, size_t s
     return e;
 }
 
-int launch_prepared(mm_ctx *ctx, Prepared &pr, const mm_launch_config &cfg_in) {
-    BatchParams &B = *pr.B;
-    if (B.nclasses == 0) return MM_OK;
-    mm_launch_config cfg = cfg_in;
+int launch_prepared(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg) {
+    if (pr.cls.empty()) return MM_OK;
     if (cfg.warps_per_block < 1 || cfg.warps_per_block > 8 || cfg.chunk_rows < 1)
         return mm_fail(ctx, MM_EBADARG, "bad launch config");
-    const size_t sm = B.warp_bytes * cfg.warps_per_block;
-    if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: %zu bytes of shared memory per CTA", sm);
-    B.chunk_rows = cfg.chunk_rows;
-    int64_t items = 0;
-    for (int i = 0; i < B.nclasses; ++i) {
-        B.prefix[i] = items;
-        const int64_t rows = B.cls[i].row_end - B.cls[i].row_begin;
-        items += (rows + cfg.chunk_rows - 1) / cfg.chunk_rows;
-    }
-    B.prefix[B.nclasses] = items;
-    B.total_items = items;
-    if (items >= (int64_t(1) << 31)) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: too many work items");
+    BatchParams *Bp = new BatchParams();
+    BatchParams &B = *Bp;
+    size_t sm = 0;
+    int rc = build_params(ctx, pr, cfg, B, sm);
+    if (rc != MM_OK) { delete Bp; return rc; }
     WsCarve wc;
-    const size_t o_q = wc.take<int>(2);
+    const size_t o_q = wc.take<int>((size_t)B.nphases + 1);
     const size_t o_fb = pr.mixed ? wc.take<u64>((size_t)pr.rows + 1) : 0;
     char *ws = mm_workspace(ctx, wc.off);
-    if (!ws) return mm_fail(ctx, MM_ENOMEM, "batched workspace of %zu bytes", wc.off);
+    if (!ws) { delete Bp; return mm_fail(ctx, MM_ENOMEM, "batched workspace of %zu bytes", wc.off); }
     B.queue = (int *)(ws + o_q);
-    B.fb_count = B.queue + 1;
+    B.fb_count = B.queue + B.nphases;
     B.fb_list = pr.mixed ? (u64 *)(ws + o_fb) : nullptr;
     cudaStream_t st = ctx->stream;
-    MM_CUDA_CHECK(ctx, cudaMemsetAsync(B.queue, 0, 2 * sizeof(int), st));
     const void *kern = pr.mixed ? (const void *)k_weights_batched<true> : (const void *)k_weights_batched<false>;
-    MM_CUDA_CHECK(ctx, mm_set_smem(ctx, kern, sm));
+    cudaError_t e = cudaMemsetAsync(B.queue, 0, sizeof(int) * (B.nphases + 1), st);
+    if (e == cudaSuccess) e = mm_set_smem(ctx, kern, sm);
     int per_sm = cfg.blocks_per_sm;
-    if (per_sm <= 0) {
+    if (e == cudaSuccess && per_sm <= 0) {
         int occ = 0;
-        MM_CUDA_CHECK(ctx, occupancy(ctx, kern, cfg.warps_per_block * 32, sm, &occ));
+        e = occupancy(ctx, kern, cfg.warps_per_block * 32, sm, &occ);
         per_sm = std::max(occ, 1);
     }
+    if (e != cudaSuccess) { delete Bp; return mm_fail(ctx, MM_ECUDA, "batched launch setup: %s", cudaGetErrorString(e)); }
     const int blocks = per_sm * ctx->num_sms;
     if (pr.mixed) k_weights_batched<true><<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
     else k_weights_batched<false><<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
-    MM_LAUNCH_CHECK(ctx);
-    if (pr.mixed) {
-        MM_CUDA_CHECK(ctx, mm_set_smem(ctx, (const void *)k_weights_batched_fallback, sm));
-        const int fb_blocks = (int)std::min<int64_t>((pr.rows + cfg.warps_per_block - 1) / cfg.warps_per_block,
-                                                     (int64_t)ctx->num_sms * 8);
-        k_weights_batched_fallback<<<std::max(fb_blocks, 1), cfg.warps_per_block * 32, sm, st>>>(B);
-        MM_LAUNCH_CHECK(ctx);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && pr.mixed) {
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / pr.fb_slot));
+        const size_t fsm = pr.fb_slot * wpb;
+        e = mm_set_smem(ctx, (const void *)k_weights_batched_fallback, fsm);
+        if (e == cudaSuccess) {
+            const int fb_blocks = (int)std::min<int64_t>((pr.rows + wpb - 1) / wpb, (int64_t)ctx->num_sms * 8);
+            k_weights_batched_fallback<<<std::max(fb_blocks, 1), wpb * 32, fsm, st>>>(B);
+            e = cudaGetLastError();
+        }
     }
+    delete Bp;
+    if (e != cudaSuccess) return mm_fail(ctx, MM_ECUDA, "batched launch: %s", cudaGetErrorString(e));
     return MM_OK;
 }
 
@@ -296,12 +349,11 @@ int mm_rbffd_weights_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *
         if (config) cfg = *config;
         else {
             auto it = ctx->tiles.find(pr.signature);
-            cfg = it != ctx->tiles.end() ? it->second : default_config(ctx, pr.B->warp_bytes);
+            cfg = it != ctx->tiles.end() ? it->second : default_config();
         }
         rc = launch_prepared(ctx, pr, cfg);
         if (rc == MM_OK) rc = run_separate(ctx, pr, jobs, precision);
     }
-    delete pr.B;
     return rc;
 }
 
@@ -318,9 +370,9 @@ int mm_autotune_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *class
     Prepared pr;
     std::vector<WeightsJob> jobs;
     int rc = prepare(ctx, nclasses, classes, precision, sample_rows, pr, jobs);
-    if (rc != MM_OK) { delete pr.B; return rc; }
+    if (rc != MM_OK) return rc;
     // full-size signature: the sample only truncates row ranges
-    mm_launch_config best_cfg = default_config(ctx, pr.B->warp_bytes);
+    mm_launch_config best_cfg = default_config();
     double best_t = 1e300;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -328,8 +380,13 @@ int mm_autotune_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *class
     const int wpbs[] = {1, 2, 4, 8};
     const int chunks[] = {4, 16, 64};
     for (int wpb : wpbs) {
-        const size_t sm = pr.B->warp_bytes * wpb;
-        if (sm > ctx->smem_optin) continue;
+        BatchParams *Bp = new BatchParams();
+        size_t sm = 0;
+        mm_launch_config probe{wpb, 1, 16};
+        const bool fits = build_params(ctx, pr, probe, *Bp, sm) == MM_OK;
+        delete Bp;
+        ctx->err.clear();
+        if (!fits || sm > ctx->smem_optin) continue;
         const void *kern = pr.mixed ? (const void *)k_weights_batched<true> : (const void *)k_weights_batched<false>;
         if (mm_set_smem(ctx, kern, sm) != cudaSuccess) { cudaGetLastError(); continue; }
         int occ = 0;
@@ -361,7 +418,6 @@ int mm_autotune_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *class
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    delete pr.B;
     if (rc != MM_OK) return rc;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return mm_fail(ctx, MM_ECUDA, "autotune: %s", cudaGetErrorString(e));
