@@ -758,22 +758,23 @@ def run_surrogate(args, rk):
     t_train = time.time() - t0
     del data
     pts, rp, col = S.make_stencils(ctx, neval, seed=10 ** 6 + rk.rank)
-    vals = {nm: torch.zeros(neval * n, dtype=torch.float64, device="cuda") for nm in ("fp64", "ir", "sur")}
+    vals = {nm: torch.zeros(neval * n, dtype=torch.float64, device="cuda")
+            for nm in ("fp64", "ir", "sur", "surir")}
     status = torch.empty(neval, dtype=torch.int32, device="cuda")
     rho = torch.empty(neval, dtype=torch.float32, device="cuda")
     tau = 1e-3
     stream = torch.cuda.current_stream(device)
 
     def run(name):
-        if name == "sur":
-            P.rbffd_weights_surrogate(ctx, net, k, m, pts, rp, col, 0, neval, n, tau, vals["sur"],
-                                      status, rho)
+        if name in ("sur", "surir"):
+            P.rbffd_weights_surrogate(ctx, net, k, m, pts, rp, col, 0, neval, n, tau, vals[name],
+                                      status, rho, fallback=P.FP64 if name == "sur" else P.FP32_IR)
         else:
             ctx.rbffd_weights(P.LAP, k, m, pts, rp, col, [vals[name]], row_end=neval, n_max=n,
                               precision=P.FP64 if name == "fp64" else P.FP32_IR)
 
     res = {}
-    for name in ("fp64", "ir", "sur"):
+    for name in ("fp64", "ir", "surir", "sur"):
         for _ in range(max(1, args.warmup)):
             run(name)
         torch.cuda.synchronize()
@@ -800,8 +801,10 @@ def run_surrogate(args, rk):
             "config": {"workload": f"surrogate: MLP 50-256x3-25 trained on {ntrain} jittered-patch "
                                    f"stencils, {neval} held-out stencils (n=25, r^5, deg 4)",
                        "tau": tau},
-            "fp64_plain": res["fp64"], "fp32_ir": res["ir"], "surrogate": res["sur"],
+            "fp64_plain": res["fp64"], "fp32_ir": res["ir"], "surrogate_fp64_fallback": res["sur"],
+            "surrogate_fp32ir_fallback": res["surir"],
             "speedup_vs_fp64_plain": res["fp64"]["ms"] / res["sur"]["ms"],
+            "speedup_fp32ir_fallback_vs_fp32ir": res["ir"]["ms"] / res["surir"]["ms"],
             "accept_fraction": float(acc.mean()),
             "error_vs_fp64": {"accepted_median": float(np.median(err[acc])) if acc.any() else None,
                               "accepted_p99": float(np.quantile(err[acc], 0.99)) if acc.any() else None,

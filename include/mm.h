@@ -323,11 +323,13 @@ int mm_mlp_load(mm_ctx *ctx, mm_mlp *net, const char *path);
  * Features of stencils: for rows [row_begin, row_end) of n nodes each,
  * d_x[(i - row_begin) * n * dim + j * dim + a] = (x_j - x_c)_a / s with
  * s = max_j ||x_j - x_c|| (FP32), d_scale[i - row_begin] = s (optional).
- * n <= 32.
+ * orient != 0 (2D): offsets in the stencil's canonical frame -- rotated so
+ * node 1 lies on +x, mirrored so node 2 has y >= 0 (Laplacian weights are
+ * invariant under both).  The surrogate path uses orient = 1.  n <= 32.
  */
 int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
                         const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end, int n,
-                        float *d_x, double *d_scale);
+                        int orient, float *d_x, double *d_scale);
 
 /*
  * Laplacian weights through the surrogate: features -> network -> scaled
@@ -337,13 +339,18 @@ int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
  * 1e-15 relative); checked against the other rows: rho = ||r - Q lambda||_inf /
  * ||l_phi||_inf with r = l_phi - A w and lambda the least-squares multipliers
  * (FP32).  rho <= tau: weights w / s^2 stored, status MM_ST_ACCEPTED;
- * otherwise the FP64 solve (status MM_ST_FALLBACK).  2D only, n == n_out of
- * the network, l <= 16.  d_rho (optional, [rows]) receives rho per row.
+ * otherwise the stencil is solved by the method itself: with
+ * fallback_precision MM_FP64 by the FP64 solve (status MM_ST_FALLBACK), with
+ * MM_FP32_IR by the FP32 + FP64-refinement solve (status MM_ST_OK), which
+ * hands its own stragglers to the FP64 solve.  The network input is the
+ * canonical-frame features (mm_stencil_features, orient = 1).  2D only,
+ * n == n_out of the network, l <= 16.  d_rho (optional, [rows]) receives rho.
  */
 int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, int64_t N,
                                const double *d_pts, const mm_csr_pattern *stencils,
                                int64_t row_begin, int64_t row_end, int n, double tau,
-                               double *d_lap_vals, int32_t *d_status, float *d_rho);
+                               int fallback_precision, double *d_lap_vals, int32_t *d_status,
+                               float *d_rho);
 
 /* ------------------------------------------------------------- measurement */
 /*

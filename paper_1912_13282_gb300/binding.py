@@ -110,10 +110,10 @@ def load():
         lib.mm_mlp_save.argtypes = [vp, vp, C.c_char_p]
         lib.mm_mlp_load.argtypes = [vp, vp, C.c_char_p]
         lib.mm_stencil_features.argtypes = [vp, C.c_int, i64, vp, C.POINTER(CsrPattern), i64, i64,
-                                            C.c_int, vp, vp]
+                                            C.c_int, C.c_int, vp, vp]
         lib.mm_rbffd_weights_surrogate.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, i64, vp,
                                                    C.POINTER(CsrPattern), i64, i64, C.c_int, dbl,
-                                                   vp, vp, vp]
+                                                   C.c_int, vp, vp, vp]
         lib.mm_apply_operator.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, dbl, vp]
         lib.mm_diffuse.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, C.c_int, vp, vp]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
@@ -400,20 +400,21 @@ class MLP:
         self.ctx._check(self._lib.mm_mlp_load(self.ctx._h, self._h, str(path).encode()))
 
 
-def stencil_features(ctx: Context, pts, row_ptr, col, row_begin, row_end, n, x, scale=None):
+def stencil_features(ctx: Context, pts, row_ptr, col, row_begin, row_end, n, x, scale=None,
+                     orient=True):
     _dev(pts, "pts", torch.float64)
     pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
     ctx._check(ctx._lib.mm_stencil_features(ctx._h, pts.shape[1], pts.shape[0], _ptr(pts),
-                                            C.byref(pat), row_begin, row_end, n, _ptr(x),
-                                            _ptr(scale)))
+                                            C.byref(pat), row_begin, row_end, n, int(orient),
+                                            _ptr(x), _ptr(scale)))
 
 
 def rbffd_weights_surrogate(ctx: Context, net: MLP, k, m, pts, row_ptr, col, row_begin, row_end, n,
-                            tau, lap_vals, status=None, rho=None):
+                            tau, lap_vals, status=None, rho=None, fallback=FP64):
     _dev(pts, "pts", torch.float64)
     _dev(lap_vals, "lap_vals", torch.float64)
     pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
     ctx._check(ctx._lib.mm_rbffd_weights_surrogate(ctx._h, net._h, k, m, pts.shape[1], pts.shape[0],
                                                    _ptr(pts), C.byref(pat), row_begin, row_end, n,
-                                                   float(tau), _ptr(lap_vals), _ptr(status),
-                                                   _ptr(rho)))
+                                                   float(tau), int(fallback), _ptr(lap_vals),
+                                                   _ptr(status), _ptr(rho)))

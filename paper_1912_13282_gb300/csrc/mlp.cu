@@ -35,6 +35,7 @@ struct mm_mlp {
     __nv_bfloat16 *dY = nullptr;        // [bmax][32]
     __nv_bfloat16 *dZa = nullptr, *dZb = nullptr;   // [bmax][256]
     float *loss = nullptr;              // [1]
+    float *part = nullptr;              // [64][256][256] split-K / bias partial sums
     float *ymean = nullptr, *ystd = nullptr;   // [32] output scaling (device)
     std::vector<float> h_mean, h_std;
     int64_t np_pad = 0;
@@ -54,10 +55,10 @@ constexpr int kH = 256, kKIN = 64, kKOUT = 32;
 // multiple of 8 and ld* multiples of 8 (16-byte vector loads); M, N arbitrary.
 constexpr int BM = 64, BN = 64, BK = 32, SPAD = 8;
 
-enum Epi { EPI_ATOMIC_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2, EPI_DGELU = 3 };
+enum Epi { EPI_PARTIAL_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2, EPI_DGELU = 3 };
 
 struct EpiParams {
-    float *c;  int ldc; float alpha;   // EPI_ATOMIC_F32 / EPI_BIAS_F32 output
+    float *c;  int ldc; float alpha;   // EPI_PARTIAL_F32 (slice z at c + z*M*ldc) / EPI_BIAS_F32 output
     const float *bias;                 // bias[n]
     float *z;  int ldz;                // pre-activation (EPI_BIAS_GELU writes, EPI_DGELU reads)
     bf16 *h;   int ldh;                // bf16 output (activation or dZ)
@@ -169,8 +170,8 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *A
                     const int c = n0 + wn * 32 + nt * 8 + 2 * t + q;
                     if (r >= M || c >= N) continue;
                     const float v = acc[mt][nt][2 * h + q];
-                    if (EPI == EPI_ATOMIC_F32) {
-                        atomicAdd(&ep.c[(int64_t)r * ep.ldc + c], ep.alpha * v);
+                    if (EPI == EPI_PARTIAL_F32) {
+                        ep.c[((int64_t)blockIdx.z * M + r) * ep.ldc + c] = ep.alpha * v;
                     } else if (EPI == EPI_BIAS_GELU) {
                         const float z = v + ep.bias[c];
                         ep.z[(int64_t)r * ep.ldz + c] = z;
@@ -186,11 +187,12 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *A
 
 template <bool AK, bool BKM, int EPI>
 int gemm(mm_ctx *ctx, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
-         const EpiParams &ep, int splits = 1) {
+         const EpiParams &ep, int splits = 1, int *slices_out = nullptr) {
     const int kslice = ((K + splits - 1) / splits + BK - 1) / BK * BK;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (K + kslice - 1) / kslice);
     k_gemm<AK, BKM, EPI><<<grid, 128, 0, ctx->stream>>>(M, N, K, A, lda, B, ldb, ep, kslice);
     MM_LAUNCH_CHECK(ctx);
+    if (slices_out) *slices_out = (int)grid.z;
     return MM_OK;
 }
 
@@ -227,13 +229,24 @@ __global__ void k_loss(const float *Y, const float *T, int64_t B, int n_out, con
     if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, s / ((float)B * n_out));
 }
 
-// db[c] += sum_r dZ[r][c] (columns across threads, rows across blocks)
-__global__ void k_bias_grad(const bf16 *dZ, int64_t B, int N, float *db) {
+// Bias-gradient partial sums: block b sums rows b, b + nblocks, ... of dZ
+// column by column into part[b][c].
+__global__ void k_bias_partial(const bf16 *dZ, int64_t B, int N, float *part) {
     const int c = threadIdx.x;
     if (c >= N) return;
     float s = 0.f;
     for (int64_t r = blockIdx.x; r < B; r += gridDim.x) s += __bfloat162float(dZ[r * N + c]);
-    atomicAdd(&db[c], s);
+    part[(int64_t)blockIdx.x * N + c] = s;
+}
+
+// out[i] = sum_z part[z][i] in z order (deterministic), i < count.
+__global__ void k_sum_parts(const float *part, int nparts, int64_t count, float *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < nparts; ++z) s += part[(int64_t)z * count + i];
+        out[i] = s;
+    }
 }
 
 // Adam (Kingma & Ba) on the FP32 master copy; refreshes the BF16 weights.
@@ -287,6 +300,23 @@ const bf16 *wmat(const mm_mlp *net, int i) {
     return net->wb + off;
 }
 
+// dW = dZ^T H (split-K partial slices, then an ordered sum) and db = column
+// sums of dZ, both deterministic.
+int weight_grads(mm_ctx *ctx, mm_mlp *net, int out, int in, int64_t B, const bf16 *dZ,
+                 const bf16 *Hin, float *dW, float *db, int splits) {
+    EpiParams e{};
+    e.c = net->part; e.ldc = in; e.alpha = 1.f;
+    int slices = 1;
+    int rc = gemm<false, false, EPI_PARTIAL_F32>(ctx, out, in, (int)B, dZ, out, Hin, in, e, splits, &slices);
+    if (rc) return rc;
+    k_sum_parts<<<grid1(ctx, (int64_t)out * in), 256, 0, ctx->stream>>>(net->part, slices, (int64_t)out * in, dW);
+    const int nb = (int)std::min<int64_t>(B, 256);
+    k_bias_partial<<<nb, out, 0, ctx->stream>>>(dZ, B, out, net->part);
+    k_sum_parts<<<grid1(ctx, out), 256, 0, ctx->stream>>>(net->part, nb, out, db);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
 // Forward pass of `B` rows already packed in net->Xb; output in net->Y.
 int forward(mm_ctx *ctx, mm_mlp *net, int64_t B) {
     EpiParams ep{};
@@ -311,21 +341,17 @@ int forward(mm_ctx *ctx, mm_mlp *net, int64_t B) {
 }
 
 // Gradients of the mean squared error w.r.t. all parameters into net->g
-// (zeroed here), for B rows with targets T (raw, [B x n_out]).
+// (every entry written, in a fixed summation order), for B rows with targets T (raw, [B x n_out]).
 int backward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *T) {
     cudaStream_t st = ctx->stream;
-    MM_CUDA_CHECK(ctx, cudaMemsetAsync(net->g, 0, sizeof(float) * net->np_pad, st));
     k_loss<<<grid1(ctx, B * kKOUT), 256, 0, st>>>(net->Y, T, B, net->n_out, net->ymean, net->ystd,
                                                    net->dY, net->loss);
     MM_LAUNCH_CHECK(ctx);
     const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
     // output layer
     const bf16 *H3 = net->Hb + 2 * net->bmax * kH;
-    EpiParams e{};
-    e.c = net->g + net->oW[3]; e.ldc = kH; e.alpha = 1.f;
-    int rc = gemm<false, false, EPI_ATOMIC_F32>(ctx, kKOUT, kH, (int)B, net->dY, kKOUT, H3, kH, e, splits);
+    int rc = weight_grads(ctx, net, kKOUT, kH, B, net->dY, H3, net->g + net->oW[3], net->g + net->ob[3], splits);
     if (rc) return rc;
-    k_bias_grad<<<std::min<int64_t>(B, 1024), kKOUT, 0, st>>>(net->dY, B, kKOUT, net->g + net->ob[3]);
     EpiParams ed{};
     ed.z = net->Z + 2 * net->bmax * kH; ed.ldz = kH; ed.h = net->dZa; ed.ldh = kH;
     rc = gemm<true, false, EPI_DGELU>(ctx, (int)B, kH, kKOUT, net->dY, kKOUT, wmat(net, 3), kH, ed);
@@ -334,12 +360,8 @@ int backward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *T) {
     for (int l = 2; l >= 0; --l) {
         const bf16 *Hin = l == 0 ? net->Xb : net->Hb + (int64_t)(l - 1) * net->bmax * kH;
         const int kin = l == 0 ? kKIN : kH;
-        EpiParams ew{};
-        ew.c = net->g + net->oW[l]; ew.ldc = kin; ew.alpha = 1.f;
-        rc = gemm<false, false, EPI_ATOMIC_F32>(ctx, kH, kin, (int)B, dZ, kH, Hin, kin, ew, splits);
+        rc = weight_grads(ctx, net, kH, kin, B, dZ, Hin, net->g + net->oW[l], net->g + net->ob[l], splits);
         if (rc) return rc;
-        k_bias_grad<<<std::min<int64_t>(B, 1024), kH, 0, st>>>(dZ, B, kH, net->g + net->ob[l]);
-        MM_LAUNCH_CHECK(ctx);
         if (l > 0) {
             EpiParams eg{};
             eg.z = net->Z + (int64_t)(l - 1) * net->bmax * kH; eg.ldz = kH; eg.h = dZn; eg.ldh = kH;
@@ -361,10 +383,14 @@ int refresh_bf16(mm_ctx *ctx, mm_mlp *net) {
 
 // ------------------------------------------------------ stencil features
 // Scaled offsets xi_j = (x_j - x_c)/s, s = max distance, of the n stencil nodes
-// in stencil order: feature row [xi_0x, xi_0y, xi_1x, ...] (FP32).
+// in stencil order: feature row [xi_0x, xi_0y, xi_1x, ...] (FP32).  With
+// `orient` (2D) the offsets are turned so the nearest other node lies on +x
+// and mirrored so the next one has y >= 0: Laplacian weights do not change
+// under rotations and reflections of the whole stencil, so the network sees
+// one canonical frame per stencil.
 template <int DIM>
 __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *col, int64_t r0,
-                           int64_t r1, int n, float *x, double *scale) {
+                           int64_t r1, int n, int orient, float *x, double *scale) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -382,9 +408,21 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
         }
         for (int o = 16; o; o >>= 1) r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
         const double s = sqrt(r2);
+        float f[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) f[a] = (float)(d[a] / s);
+        if (DIM == 2 && orient && n >= 3) {
+            const float ax = __shfl_sync(0xffffffffu, f[0], 1), ay = __shfl_sync(0xffffffffu, f[1], 1);
+            const float an = sqrtf(ax * ax + ay * ay);
+            const float c = an > 0.f ? ax / an : 1.f, sn = an > 0.f ? ay / an : 0.f;
+            const float xr = c * f[0] + sn * f[1], yr = -sn * f[0] + c * f[1];
+            const float y2 = __shfl_sync(0xffffffffu, yr, 2);
+            f[0] = xr;
+            f[1] = y2 < 0.f ? -yr : yr;
+        }
         if (lane < n) {
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) x[(row - r0) * (int64_t)n * DIM + lane * DIM + a] = (float)(d[a] / s);
+            for (int a = 0; a < DIM; ++a) x[(row - r0) * (int64_t)n * DIM + lane * DIM + a] = f[a];
         }
         if (lane == 0 && scale) scale[row - r0] = s;
     }
@@ -406,20 +444,6 @@ struct ProjParams {
     float *rho_out;         // optional [rows]
 };
 
-// Cholesky-based solve of (D G D) v = rhs in place (lane 0; l <= 16).
-__device__ void chol_solve(const float (*Lg)[17], float *v, int l) {
-    for (int i = 0; i < l; ++i) {
-        float t = v[i];
-        for (int j = 0; j < i; ++j) t -= Lg[i][j] * v[j];
-        v[i] = t / Lg[i][i];
-    }
-    for (int i = l - 1; i >= 0; --i) {
-        float t = v[i];
-        for (int j = i + 1; j < l; ++j) t -= Lg[j][i] * v[j];
-        v[i] = t / Lg[i][i];
-    }
-}
-
 template <int DIM>
 __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjParams J) {
     constexpr int NM = 32, LM = 16;
@@ -429,12 +453,13 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
     __shared__ float s_xi32[4][NM * DIM];
     __shared__ double s_Q[4][NM][LM + 1];
     __shared__ float s_Q32[4][NM][LM + 1];
-    __shared__ float s_G[4][LM][LM + 1];
+    __shared__ float s_G[4][LM][2 * LM + 1];    // [D G D | I] -> [I | (D G D)^-1]
     __shared__ double s_w[4][NM];
     __shared__ float s_w32[4][NM], s_r[4][NM];
-    __shared__ float s_v[4][LM], s_d[4][LM];
+    __shared__ float s_z[4][LM], s_d[4][LM], s_m[4][LM];
     double *xi = s_xi[wib];
     float *x32 = s_xi32[wib];
+    float (*G)[2 * LM + 1] = s_G[wib];
     const int l = P.l, di = DIM - 2, k = P.k;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -462,60 +487,65 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             s_w[wib][lane] = (double)J.wt[(row - P.row_begin) * n + lane];
         }
         __syncwarp();
-        // Gram matrix Q^T Q (FP32), Jacobi scaling D = diag(G)^-1/2, Cholesky D G D = L L^T
+        // Gram matrix Q^T Q (FP32) with Jacobi scaling D = diag^-1/2, and its
+        // inverse by Gauss-Jordan on [D G D | I] (symmetric positive definite:
+        // no pivoting)
         for (int e = lane; e < l * l; e += 32) {
             const int a = e / l, b = e % l;
             float acc = 0.f;
             for (int j = 0; j < n; ++j) acc = fmaf(s_Q32[wib][j][a], s_Q32[wib][j][b], acc);
-            s_G[wib][a][b] = acc;
+            G[a][b] = acc;
+            G[a][l + b] = a == b ? 1.f : 0.f;
         }
         __syncwarp();
-        if (lane < l) s_d[wib][lane] = rsqrtf(fmaxf(s_G[wib][lane][lane], 1e-30f));
+        if (lane < l) s_d[wib][lane] = rsqrtf(fmaxf(G[lane][lane], 1e-30f));
         __syncwarp();
         for (int e = lane; e < l * l; e += 32) {
             const int a = e / l, b = e % l;
-            s_G[wib][a][b] *= s_d[wib][a] * s_d[wib][b];
+            G[a][b] *= s_d[wib][a] * s_d[wib][b];
         }
         __syncwarp();
         bool ok = true;
         for (int c = 0; c < l; ++c) {
-            const float dcc = s_G[wib][c][c];
-            ok &= dcc > 0.f;
-            const float ld = sqrtf(fmaxf(dcc, 1e-30f));
+            const float piv = G[c][c];
+            ok &= piv > 0.f;
+            const float ip = piv > 0.f ? 1.f / piv : 0.f;
             __syncwarp();
-            if (lane > c && lane < l) s_G[wib][lane][c] /= ld;
-            if (lane == 0) s_G[wib][c][c] = ld;
+            for (int e = lane; e < 2 * l; e += 32) G[c][e] *= ip;
+            if (lane < l) s_m[wib][lane] = G[lane][c];     // multipliers, read before the update
             __syncwarp();
-            const int w = l - c - 1;
-            for (int e = lane; e < w * w; e += 32) {
-                const int i = c + 1 + e / w, j = c + 1 + e % w;
-                if (j <= i) s_G[wib][i][j] -= s_G[wib][i][c] * s_G[wib][j][c];
+            for (int e = lane; e < l * 2 * l; e += 32) {
+                const int i = e / (2 * l), j = e % (2 * l);
+                if (i != c) G[i][j] = fmaf(-s_m[wib][i], G[c][j], G[i][j]);
             }
             __syncwarp();
         }
-        // FP64 constraint residual c = l_q - Q^T w, FP32 correction w += Q D (DGD)^-1 D c
-        for (int pass = 0; pass < 4; ++pass) {
+        // Correction passes: FP64 constraint residual c = l_q - Q^T w (all
+        // lanes: lane = b + 16 h sums half h of the nodes), z = D Ginv D c in
+        // FP32, w += Q z in FP64 (so w - wt stays in range(Q)).
+        const int bl = lane & 15, hl = lane >> 4, jh = (n + 1) / 2;
+        for (int pass = 0; pass < 5; ++pass) {
             double cb = 0.0, sc = 0.0;
-            if (lane < l) {
-                cb = (double)c_mono.lap[di][lane];
-                for (int j = 0; j < n; ++j) {
-                    const double t = s_Q[wib][j][lane] * s_w[wib][j];
+            if (bl < l)
+                for (int j = hl * jh; j < min(n, (hl + 1) * jh); ++j) {
+                    const double t = s_Q[wib][j][bl] * s_w[wib][j];
                     cb -= t;
                     sc += fabs(t);
                 }
-            }
-            double cm = fabs(cb) / fmax(1.0, sc);
+            cb += __shfl_xor_sync(0xffffffffu, cb, 16);
+            sc += __shfl_xor_sync(0xffffffffu, sc, 16);
+            if (bl < l) cb += (double)c_mono.lap[di][bl];
+            double cm = (bl < l) ? fabs(cb) / fmax(1.0, sc) : 0.0;
             for (int o = 16; o; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
             if (cm <= 1e-15) break;
-            if (lane < l) s_v[wib][lane] = (float)cb * s_d[wib][lane];
-            __syncwarp();
-            if (lane == 0) chol_solve(s_G[wib], s_v[wib], l);
+            const float dc = bl < l ? (float)cb * s_d[wib][bl] : 0.f;
+            float zb = 0.f;
+            for (int a = 0; a < l; ++a) zb = fmaf(G[bl < l ? bl : 0][l + a], __shfl_sync(0xffffffffu, dc, a), zb);
+            if (lane < l) s_z[wib][lane] = zb * s_d[wib][lane];
             __syncwarp();
             if (lane < n) {
-                // FP64, so w - wt stays in range(Q) to FP64 rounding (the exact
-                // least-norm correction)
                 double corr = 0.0;
-                for (int b = 0; b < l; ++b) corr = fma(s_Q[wib][lane][b], (double)(s_v[wib][b] * s_d[wib][b]), corr);
+                for (int b = 0; b < l; ++b) corr = fma(s_Q[wib][lane][b], (double)s_z[wib][b], corr);
                 s_w[wib][lane] += corr;
             }
             __syncwarp();
@@ -544,18 +574,18 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             s_r[wib][lane] = lphi - aw;
         }
         __syncwarp();
-        if (lane < l) {
-            float qr = 0.f;
+        float qr = 0.f;
+        if (lane < l)
             for (int j = 0; j < n; ++j) qr = fmaf(s_Q32[wib][j][lane], s_r[wib][j], qr);
-            s_v[wib][lane] = qr * s_d[wib][lane];
-        }
-        __syncwarp();
-        if (lane == 0) chol_solve(s_G[wib], s_v[wib], l);
+        const float dq = lane < l ? qr * s_d[wib][lane] : 0.f;
+        float lam = 0.f;
+        for (int a = 0; a < l; ++a) lam = fmaf(G[lane < l ? lane : 0][l + a], __shfl_sync(0xffffffffu, dq, a), lam);
+        if (lane < l) s_z[wib][lane] = lam * s_d[wib][lane];
         __syncwarp();
         float e = 0.f;
         if (lane < n) {
             float ql = 0.f;
-            for (int b = 0; b < l; ++b) ql = fmaf(s_Q32[wib][lane][b], s_v[wib][b] * s_d[wib][b], ql);
+            for (int b = 0; b < l; ++b) ql = fmaf(s_Q32[wib][lane][b], s_z[wib][b], ql);
             e = fabsf(s_r[wib][lane] - ql);
         }
         float emax = e, lmax = fabsf(lphi);
@@ -574,6 +604,27 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             const int slot = atomicAdd(J.fb_count, 1);
             J.fb_list[slot] = (int)row;
             if (P.status) P.status[row] = MM_ST_NONCONVERGED;
+        }
+        __syncwarp();
+    }
+}
+
+// the FP32 + FP64-refinement solver for stencils the residual check rejected;
+// its own stragglers go on to the FP64 solver through a second queue
+template <int DIM, int RPL>
+__global__ void __launch_bounds__(128) k_surrogate_fallback_mixed(WParams P, int *list2, int *count2) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const MixedLayout Ly = mixed_layout(P.n_max, P.l, 1, DIM);
+    char *base = (char *)smem + (size_t)wib * Ly.bytes;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t count = *P.list_count;
+    for (int64_t t = gw; t < count; t += nw) {
+        const int64_t row = (int64_t)P.list[t];
+        if (mixed_row<DIM, RPL, 1>(P, row, base) && lane == 0) {
+            const int slot = atomicAdd(count2, 1);
+            list2[slot] = (int)row;
         }
         __syncwarp();
     }
@@ -655,7 +706,8 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     }
     net->np_pad = off;
     const int64_t B = net->bmax;
-    size_t bytes_f = sizeof(float) * (size_t)(4 * off + 3 * B * kH + B * kKOUT + 1 + 2 * kKOUT);
+    const size_t npart = (size_t)64 * kH * kH;
+    size_t bytes_f = sizeof(float) * (size_t)(4 * off + 3 * B * kH + B * kKOUT + 1 + 2 * kKOUT + npart);
     size_t bytes_h = sizeof(bf16) * (size_t)(wsz[0] + wsz[1] + wsz[2] + wsz[3] + 3 * B * kH + B * kKIN +
                                              B * kKOUT + 2 * B * kH);
     char *fb = nullptr, *hb = nullptr;
@@ -674,7 +726,8 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     net->Y = f; f += B * kKOUT;
     net->loss = f; f += 1;
     net->ymean = f; f += kKOUT;
-    net->ystd = f;
+    net->ystd = f; f += kKOUT;
+    net->part = f;
     bf16 *h = (bf16 *)hb;
     net->wb = h; h += wsz[0] + wsz[1] + wsz[2] + wsz[3];
     net->Hb = h; h += 3 * B * kH;
@@ -880,7 +933,7 @@ int mm_mlp_load(mm_ctx *ctx, mm_mlp *net, const char *path) {
 
 int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
                         const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end, int n,
-                        float *d_x, double *d_scale) {
+                        int orient, float *d_x, double *d_scale) {
     if (!ctx) return MM_EBADARG;
     ctx->err.clear();
     if ((dim != 2 && dim != 3) || N < 1 || !d_pts || !stencils || !stencils->d_row_ptr ||
@@ -891,8 +944,8 @@ int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
     const int64_t rows = row_end - row_begin;
     if (rows == 0) return MM_OK;
     const int blocks = (int)std::min<int64_t>((rows + 3) / 4, (int64_t)ctx->num_sms * 32);
-    if (dim == 2) k_features<2><<<blocks, 128, 0, ctx->stream>>>(d_pts, stencils->d_row_ptr, stencils->d_col, row_begin, row_end, n, d_x, d_scale);
-    else k_features<3><<<blocks, 128, 0, ctx->stream>>>(d_pts, stencils->d_row_ptr, stencils->d_col, row_begin, row_end, n, d_x, d_scale);
+    if (dim == 2) k_features<2><<<blocks, 128, 0, ctx->stream>>>(d_pts, stencils->d_row_ptr, stencils->d_col, row_begin, row_end, n, orient, d_x, d_scale);
+    else k_features<3><<<blocks, 128, 0, ctx->stream>>>(d_pts, stencils->d_row_ptr, stencils->d_col, row_begin, row_end, n, orient, d_x, d_scale);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }
@@ -900,12 +953,15 @@ int mm_stencil_features(mm_ctx *ctx, int dim, int64_t N, const double *d_pts,
 int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, int64_t N,
                                const double *d_pts, const mm_csr_pattern *stencils,
                                int64_t row_begin, int64_t row_end, int n, double tau,
-                               double *d_lap_vals, int32_t *d_status, float *d_rho) {
+                               int fallback_precision, double *d_lap_vals, int32_t *d_status,
+                               float *d_rho) {
     if (!ctx || !net) return MM_EBADARG;
     ctx->err.clear();
     if (dim != 2 || n * dim != net->n_in || n != net->n_out)
         return mm_fail(ctx, MM_EBADARG, "the network expects 2D stencils of %d nodes", net->n_out);
     if (!(tau > 0)) return mm_fail(ctx, MM_EBADARG, "tau must be > 0");
+    if (fallback_precision != MM_FP64 && fallback_precision != MM_FP32_IR)
+        return mm_fail(ctx, MM_EBADARG, "fallback precision must be MM_FP64 or MM_FP32_IR");
     double *vals[1] = {d_lap_vals};
     WeightsJob job{};
     int rc = weights_job_from_args(ctx, MM_LAP, k, m, dim, N, d_pts, nullptr, stencils, row_begin,
@@ -920,17 +976,18 @@ int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, 
     WsCarve wc;
     const size_t o_x = wc.take<float>((size_t)std::min(rows, chunk) * n * dim);
     const size_t o_y = wc.take<float>((size_t)std::min(rows, chunk) * n);
-    const size_t o_cnt = wc.take<int>(1);
+    const size_t o_cnt = wc.take<int>(2);
     const size_t o_list = wc.take<int>((size_t)rows);
+    const size_t o_list2 = wc.take<int>((size_t)rows);
     char *ws = mm_workspace(ctx, wc.off);
     if (!ws) return mm_fail(ctx, MM_ENOMEM, "surrogate workspace of %zu bytes", wc.off);
     float *x = (float *)(ws + o_x), *y = (float *)(ws + o_y);
-    int *cnt = (int *)(ws + o_cnt), *list = (int *)(ws + o_list);
+    int *cnt = (int *)(ws + o_cnt), *list = (int *)(ws + o_list), *list2 = (int *)(ws + o_list2);
     cudaStream_t st = ctx->stream;
-    MM_CUDA_CHECK(ctx, cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
     for (int64_t r0 = row_begin; r0 < row_end; r0 += chunk) {
         const int64_t r1 = std::min(row_end, r0 + chunk);
-        rc = mm_stencil_features(ctx, dim, N, d_pts, stencils, r0, r1, n, x, nullptr);
+        rc = mm_stencil_features(ctx, dim, N, d_pts, stencils, r0, r1, n, 1, x, nullptr);
         if (rc != MM_OK) return rc;
         rc = mm_mlp_forward(ctx, net, r1 - r0, x, y);
         if (rc != MM_OK) return rc;
@@ -947,10 +1004,27 @@ int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, 
         k_project<2><<<blocks, 128, 0, st>>>(J);
         MM_LAUNCH_CHECK(ctx);
     }
-    // rejected stencils: FP64 solve
+    // rejected stencils: FP32 + FP64 refinement first if asked, then FP64
     WParams F = P;
     F.list = list;
     F.list_count = cnt;
+    if (fallback_precision == MM_FP32_IR) {
+        const MixedLayout Ly = mixed_layout(P.n_max, P.l, 1, dim);
+        const int mw = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / Ly.bytes));
+        const size_t msm = Ly.bytes * mw;
+        const int rpl = (P.M_max + 31) / 32;
+        const void *mk = rpl <= 1 ? (const void *)k_surrogate_fallback_mixed<2, 1>
+                                  : (rpl == 2 ? (const void *)k_surrogate_fallback_mixed<2, 2>
+                                              : (const void *)k_surrogate_fallback_mixed<2, 3>);
+        MM_CUDA_CHECK(ctx, mm_set_smem(ctx, mk, msm));
+        const int mblocks = (int)std::min<int64_t>((rows + mw - 1) / mw, (int64_t)ctx->num_sms * 32);
+        if (rpl <= 1) k_surrogate_fallback_mixed<2, 1><<<mblocks, mw * 32, msm, st>>>(F, list2, cnt + 1);
+        else if (rpl == 2) k_surrogate_fallback_mixed<2, 2><<<mblocks, mw * 32, msm, st>>>(F, list2, cnt + 1);
+        else k_surrogate_fallback_mixed<2, 3><<<mblocks, mw * 32, msm, st>>>(F, list2, cnt + 1);
+        MM_LAUNCH_CHECK(ctx);
+        F.list = list2;
+        F.list_count = cnt + 1;
+    }
     const size_t w64 = fp64_warp_doubles(F.M_max, F.pitch64, F.n_max, dim) * sizeof(double);
     const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / w64));
     const size_t sm = w64 * wpb;

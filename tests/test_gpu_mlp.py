@@ -143,6 +143,12 @@ def test_surrogate_weights_path(P, ctx, oracle, trained):
     P.rbffd_weights_surrogate(ctx, net, k, m, pts, rp, col, 0, count, n, tau, vals, status, rho)
     ref = torch.zeros_like(vals)
     ctx.rbffd_weights(P.LAP, k, m, pts, rp, col, [ref], row_end=count, n_max=n, precision=P.FP64)
+    refir = torch.zeros_like(vals)
+    ctx.rbffd_weights(P.LAP, k, m, pts, rp, col, [refir], row_end=count, n_max=n, precision=P.FP32_IR)
+    vir = torch.zeros_like(vals)
+    stir = torch.empty_like(status)
+    P.rbffd_weights_surrogate(ctx, net, k, m, pts, rp, col, 0, count, n, tau, vir, stir,
+                              fallback=P.FP32_IR)
     torch.cuda.synchronize()
     st, w, w64 = status.cpu().numpy(), vals.cpu().numpy(), ref.cpu().numpy()
     r = rho.cpu().numpy()
@@ -152,6 +158,16 @@ def test_surrogate_weights_path(P, ctx, oracle, trained):
     assert acc.mean() > 0.2, acc.mean()
     assert np.array_equal(w.reshape(count, n)[fb], w64.reshape(count, n)[fb])
     assert (r[acc] <= tau).all()
+    # FP32+IR fallback: same accepted rows and weights; the rejected rows
+    # equal the FP32+IR solve (or the FP64 one for its own stragglers)
+    st2, w2, wir = stir.cpu().numpy(), vir.cpu().numpy(), refir.cpu().numpy()
+    assert np.array_equal(st2 == P.binding.ST_ACCEPTED, acc)
+    assert np.array_equal(w2.reshape(count, n)[acc], w.reshape(count, n)[acc])
+    rej_ok = (st2 == P.binding.ST_OK)
+    rej_fb = (st2 == P.binding.ST_FALLBACK)
+    assert (acc | rej_ok | rej_fb).all()
+    assert np.array_equal(w2.reshape(count, n)[rej_ok], wir.reshape(count, n)[rej_ok])
+    assert np.array_equal(w2.reshape(count, n)[rej_fb], w64.reshape(count, n)[rej_fb])
     pts_h, rp_h, col_h = pts.cpu().numpy(), rp.cpu().numpy(), col.cpu().numpy()
     pred_h, s_h = pred.cpu().numpy().astype(np.float64), scale.cpu().numpy()
     from _helpers import monomial_residual
