@@ -4,8 +4,9 @@ Default workload (the one the headline metric is quoted on): the 1,000,000-node
 2D unit disk minus 5 holes; interior nodes get 25-node stencils with PHS r^5 +
 degree-4 monomials (Laplacian, d/dx, d/dy), boundary nodes 30-node stencils
 with d/dn.  One step = the whole hot path over the node set: grid binning +
-kNN stencils, weights for both classes in the chosen form (FP32 LU with FP64
-refinement and FP64 fallback), one application of each assembled operator.
+kNN stencils, weights for both classes in the chosen form (FP32 Gauss-Jordan
+inverse with FP64 refinement and FP64 fallback), one application of each
+assembled operator.
 The plain FP64 GPU path is timed the same way beside it; the sampled error
 against the CPU oracle and the Poisson solution error of both weight sets are
 reported with it.
@@ -517,7 +518,7 @@ def run_disk(args, rk):
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12,
             "unit": "TFLOP/s", "frac": achieved / fp64_peak,
             "traffic": None if traffic is None else traffic["bytes_per_row"] * Ni,
-            "kernel": "k_weights_mixed<2,2,3> (interior rows; FP32 LU + FP64 refinement)",
+            "kernel": "k_weights_mixed<2,2,3> (interior rows; FP32 inverse + FP64 refinement)",
             "algorithmic": "FP64 flops per interior stencil: A block, Q, RHS, one full residual, "
                            "constraint residual, updates (bench.mixed_fp64_flops)",
             "peak_source": "FP64 FMA peak measured in this run (mm_measure_fma_peak); "
@@ -528,7 +529,7 @@ def run_disk(args, rk):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": DISK["workload"], "N": ns.N,
-                       "precision": "fp32 LU + fp64 refinement (fp64 fallback)",
+                       "precision": "fp32 inverse + fp64 refinement (fp64 fallback)",
                        "l2": "256 MiB buffer written between timed steps",
                        "step": "grid kNN + weights (2 classes) + 3 operator applications"},
             "fp64_plain": {"value": throughput(n_all, ms64, args.steps), "unit": "nodes/s",

@@ -58,8 +58,9 @@ extern "C" {
 
 /* ------------------------------------------------------------ precisions */
 #define MM_FP64 0     /* plain FP64 solve                                      */
-#define MM_FP32_IR 1  /* FP32 LU + FP64-residual iterative refinement,
-                         condition-estimate / non-convergence fallback to FP64 */
+#define MM_FP32_IR 1  /* FP32 Gauss-Jordan inverse + FP64-residual iterative
+                         refinement (at least two steps); condition-number /
+                         non-convergence fallback to FP64                      */
 
 /* ------------------------------------------------------------ kNN methods */
 #define MM_KNN_AUTO 0
@@ -68,8 +69,11 @@ extern "C" {
 
 /* ------------------------------------------------------------ ctx options */
 #define MM_OPT_IR_TOL 1        /* IR stop: estimated rel. forward error (1e-9) */
-#define MM_OPT_IR_MAX_STEPS 2  /* IR residual evaluations at most (4)          */
-#define MM_OPT_KAPPA_MAX 3     /* fallback if kappa1_est * u32 exceeds (0.1)   */
+#define MM_OPT_IR_MAX_STEPS 2  /* IR residual evaluations at most (4); below 2
+                                  every stencil goes to the FP64 solve        */
+#define MM_OPT_KAPPA_MAX 3     /* fallback if kappa1 * u32 exceeds (0.1);
+                                  kappa1 = ||K||_1 ||K^-1||_1, the second norm
+                                  taken exactly from the FP32 inverse         */
 
 typedef struct mm_ctx mm_ctx;
 

@@ -87,7 +87,6 @@ int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, in
                            int *fb_list) {
     const int dim = job.dim;
     WParams P = wparams_from_job(ctx, job);
-    const int R = P.R;
     if (P.M_max > kMaxM) return mm_fail(ctx, MM_EUNSUPPORTED, "n_max + l = %d > %d", P.M_max, kMaxM);
     const int64_t rows = job.row_end - job.row_begin;
     if (rows <= 0) return MM_OK;
@@ -118,7 +117,7 @@ int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, in
     };
     if (precision == MM_FP64) return launch_fp64(nullptr, nullptr, rows);
 
-    // mixed: FP32 LU + FP64-residual refinement, queue stragglers for FP64
+    // mixed: FP32 inverse + FP64-residual refinement, queue stragglers for FP64
     if (fb_count && fb_list) {
         P.fb_count = fb_count;
         P.fb_list = fb_list;

@@ -342,141 +342,259 @@ __device__ __noinline__ void fp64_row(const WParams &P, int64_t row, double *bas
 }
 
 // ------------------------------------------------------------ mixed solver
-// FP32 LU with implicit partial pivoting: rows are never exchanged; the row
-// chosen at step kk is marked (step = kk) and copied to a per-warp buffer
-// from which the remaining rows are updated.  Lane t owns rows t, t+32, t+64
-// (RPL of them).  A32 [M x p32] (row-major, p32 odd) holds L below the pivots
-// and U in the pivot rows; A32[perm[kk]][kk] holds 1/U_kk.
+// FP32 Gauss-Jordan inversion with implicit partial pivoting.  Rows are never
+// exchanged: the row chosen at step kk is marked (step = kk, perm[kk] = row).
+// Lane t owns rows t, t+32, ... (RPL of them).  S [M x p32] (row-major, p32 a
+// multiple of 4 with p32/4 odd, so float4 accesses of 8 consecutive rows hit
+// distinct banks) holds K on entry, with zeros in the padding columns
+// M .. 4*ceil(M/4)-1.  In-place elimination of column kk from every other row
+// leaves, in that column, the matching column of the inverse; at the end
+//     (K^-1)[i][j] = S[perm[i]][step of row j].
+// Columns are eliminated two at a time: the second pivot is chosen from
+// column kk+1 as updated by the first step (one column only), then every
+// other row takes both rank-1 updates in one pass over its entries.
+// Returns false if a pivot is not larger than `tiny`.
 constexpr int kBig = 1 << 30;
 
+// d = a * b + c on two FP32 lanes at once (Blackwell packed FP32 FMA)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)),
+          "l"(*reinterpret_cast<unsigned long long *>(&c)));
+    return *reinterpret_cast<float2 *>(&d);
+}
+
+// Warp-wide argmax of |v| over the lanes' candidate rows (row < 96): one
+// redux of the key |v| (low 7 mantissa bits dropped) : (127 - row), so ties
+// go to the lower row.  Returns the row (kBig if there is no candidate).
+__device__ __forceinline__ int pivot_row(unsigned key) {
+    const unsigned best = __reduce_max_sync(kFull, key);
+    return best ? 127 - (int)(best & 0x7Fu) : kBig;
+}
+__device__ __forceinline__ unsigned pivot_key(float v, int r) {
+    return (__float_as_uint(fabsf(v)) & 0xFFFFFF80u) | (unsigned)(127 - r);
+}
+
 template <int RPL>
-__device__ bool lu32_implicit(float *A, int p32, int M, int *step, int *perm, float *ubuf,
-                              float tiny) {
+__device__ bool gj32_invert(float *__restrict__ S, int p32, int M, int *step, int *perm,
+                            float *__restrict__ ubuf, float tiny) {
     const int lane = threadIdx.x & 31;
+    const int C4 = (M + 3) >> 2, W4 = 4 * C4;
+    float *__restrict__ ubuf2 = ubuf + W4;
     bool ok = true;
-    for (int kk = 0; kk < M; ++kk) {
-        float best = -1.0f;
-        int brow = kBig;
+    int kk = 0;
+    for (; kk + 1 < M; kk += 2) {
+        // first pivot: column kk
+        unsigned key = 0;
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            if (step[q] == kBig) {
-                const int r = lane + 32 * q;
-                const float v = fabsf(A[r * p32 + kk]);
-                if (v > best) { best = v; brow = r; }
-            }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const float ob = __shfl_xor_sync(kFull, best, o);
-            const int orow = __shfl_xor_sync(kFull, brow, o);
-            if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
-        }
-        const bool good = best > tiny;
-        ok &= good;
-        if (brow == kBig) brow = 0;               // only when every row is exhausted (not reached)
-        // pivot row from the even column c0 <= kk+1 on, zeros at columns <= kk, so
-        // the updates below can run on column pairs
-        const int c0 = (kk + 1) & ~1;
-        const float *Up = A + brow * p32;
-        for (int c = c0 + lane; c < p32; c += 32) ubuf[c] = (c > kk && c < M) ? Up[c] : 0.0f;
-        const float piv = Up[kk];
-        if (lane == 0) perm[kk] = brow;
-        __syncwarp();
-        const float ip = good ? 1.0f / piv : 0.0f;
-        float l[RPL];
+        for (int q = 0; q < RPL; ++q)
+            if (step[q] == kBig) key = max(key, pivot_key(S[(lane + 32 * q) * p32 + kk], lane + 32 * q));
+        int p1 = pivot_row(key);
+        if (p1 == kBig) p1 = 0;                    // only when every row is exhausted (not reached)
+        const float piv1 = S[p1 * p32 + kk];
+        const bool good1 = fabsf(piv1) > tiny;
+        const float ip1 = good1 ? __frcp_rn(piv1) : 0.0f;
+        const float u1n = S[p1 * p32 + kk + 1] * ip1;          // u1 at column kk+1
+        // own rows: multiplier of step 1 and column kk+1 after step 1
+        float m1[RPL], c1[RPL];
+        unsigned key2 = 0;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             const int r = lane + 32 * q;
-            if (r == brow) { step[q] = kk; A[r * p32 + kk] = ip; }
-            l[q] = 0.0f;
-            if (step[q] == kBig) {
-                l[q] = A[r * p32 + kk] * ip;
-                A[r * p32 + kk] = l[q];
+            m1[q] = 0.0f;
+            c1[q] = 0.0f;
+            if (r < M) {
+                if (r == p1) {
+                    step[q] = kk;
+                    c1[q] = u1n;
+                } else {
+                    m1[q] = S[r * p32 + kk];
+                    c1[q] = fmaf(-m1[q], u1n, S[r * p32 + kk + 1]);
+                    if (step[q] == kBig) key2 = max(key2, pivot_key(c1[q], r));
+                }
             }
         }
+        // second pivot: column kk+1 after step 1
+        int p2 = pivot_row(key2);
+        if (p2 == kBig) p2 = p1 == 0 ? 1 : 0;      // not reached
+        const float m1p2 = S[p2 * p32 + kk];
+        const float piv2 = fmaf(-m1p2, u1n, S[p2 * p32 + kk + 1]);
+        const bool good2 = fabsf(piv2) > tiny;
+        ok &= good1 && good2;
+        const float ip2 = good2 ? __frcp_rn(piv2) : 0.0f;
+        const float u2k = -m1p2 * ip1 * ip2;                   // u2 at column kk
+        const float m2p1 = u1n;                                // step-2 multiplier of row p1
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (lane + 32 * q == p2) step[q] = kk + 1;
         __syncwarp();
-        const float2 *u2 = reinterpret_cast<const float2 *>(ubuf);
-        for (int c = c0; c < M; c += 2) {
-            const float2 u = u2[c >> 1];
+        // the two scaled pivot rows (0 at columns kk, kk+1) and rows p1, p2 themselves
+        float *P1 = S + p1 * p32, *P2 = S + p2 * p32;
+        for (int c = lane; c < W4; c += 32) {
+            const float a1 = P1[c], a2 = P2[c];
+            const float u1 = a1 * ip1;
+            const float u2 = fmaf(-m1p2, u1, a2) * ip2;
+            const bool piv_col = c == kk || c == kk + 1;
+            ubuf[c] = piv_col ? 0.0f : u1;
+            ubuf2[c] = piv_col ? 0.0f : u2;
+            P2[c] = c == kk ? u2k : (c == kk + 1 ? ip2 : u2);
+            P1[c] = c == kk ? fmaf(-m2p1, u2k, ip1) : (c == kk + 1 ? -m2p1 * ip2 : fmaf(-m2p1, u2, u1));
+        }
+        if (lane == 0) {
+            perm[kk] = p1;
+            perm[kk + 1] = p2;
+        }
+        __syncwarp();
+        bool live[RPL];
+        float2 n1[RPL], n2[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            live[q] = r < M && r != p1 && r != p2;
+            n1[q] = make_float2(-m1[q], -m1[q]);
+            n2[q] = make_float2(-c1[q], -c1[q]);
+        }
+        const float4 *u4 = reinterpret_cast<const float4 *>(ubuf);
+        const float4 *v4 = reinterpret_cast<const float4 *>(ubuf2);
+#pragma unroll 2
+        for (int c4 = 0; c4 < C4; ++c4) {
+            const float4 u = u4[c4], v = v4[c4];
 #pragma unroll
             for (int q = 0; q < RPL; ++q)
-                if (step[q] == kBig) {
-                    float2 *dst = reinterpret_cast<float2 *>(A + (lane + 32 * q) * p32 + c);
-                    float2 a = *dst;
-                    a.x = fmaf(-l[q], u.x, a.x);
-                    a.y = fmaf(-l[q], u.y, a.y);
-                    *dst = a;
+                if (live[q]) {
+                    float4 *dst = reinterpret_cast<float4 *>(S + (lane + 32 * q) * p32) + c4;
+                    const float4 a = *dst;
+                    float2 lo = ffma2(n1[q], make_float2(u.x, u.y), make_float2(a.x, a.y));
+                    float2 hi = ffma2(n1[q], make_float2(u.z, u.w), make_float2(a.z, a.w));
+                    lo = ffma2(n2[q], make_float2(v.x, v.y), lo);
+                    hi = ffma2(n2[q], make_float2(v.z, v.w), hi);
+                    *dst = make_float4(lo.x, lo.y, hi.x, hi.y);
                 }
         }
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (live[q]) {
+                float *Sr = S + (lane + 32 * q) * p32;
+                Sr[kk] = fmaf(-c1[q], u2k, -m1[q] * ip1);
+                Sr[kk + 1] = -c1[q] * ip2;
+            }
+        __syncwarp();
+    }
+    if (kk < M) {
+        // last column of an odd-sized system: one rank-1 step
+        unsigned key = 0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (step[q] == kBig) key = max(key, pivot_key(S[(lane + 32 * q) * p32 + kk], lane + 32 * q));
+        int p1 = pivot_row(key);
+        if (p1 == kBig) p1 = 0;
+        const float piv = S[p1 * p32 + kk];
+        const bool good = fabsf(piv) > tiny;
+        ok &= good;
+        const float ip = good ? __frcp_rn(piv) : 0.0f;
+        float2 mm[RPL];
+        bool live[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            live[q] = r < M && r != p1;
+            const float m = live[q] ? S[r * p32 + kk] : 0.0f;
+            mm[q] = make_float2(-m, -m);
+            if (r == p1) step[q] = kk;
+        }
+        __syncwarp();
+        float *Pr = S + p1 * p32;
+        for (int c = lane; c < W4; c += 32) {
+            const float v = Pr[c] * ip;
+            ubuf[c] = c == kk ? 0.0f : v;
+            Pr[c] = c == kk ? ip : v;
+        }
+        if (lane == 0) perm[kk] = p1;
+        __syncwarp();
+        const float4 *u4 = reinterpret_cast<const float4 *>(ubuf);
+        for (int c4 = 0; c4 < C4; ++c4) {
+            const float4 u = u4[c4];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q)
+                if (live[q]) {
+                    float4 *dst = reinterpret_cast<float4 *>(S + (lane + 32 * q) * p32) + c4;
+                    const float4 a = *dst;
+                    const float2 lo = ffma2(mm[q], make_float2(u.x, u.y), make_float2(a.x, a.y));
+                    const float2 hi = ffma2(mm[q], make_float2(u.z, u.w), make_float2(a.z, a.w));
+                    *dst = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (live[q]) S[(lane + 32 * q) * p32 + kk] = mm[q].x * ip;
         __syncwarp();
     }
     return ok;
 }
 
-// Solve K x = b for R right-hand sides with the factors above.  z holds b
-// by row for the lane's own rows (consumed).  The solution x, by column, is
-// written to X [M x R] (shared) and returned after a warp barrier.
+// x = K^-1 b for R right-hand sides with the inverse above.  V [M x R]
+// (shared, natural row order) holds b on entry and x on exit; Bp [4*ceil(M/4)
+// x R] (shared, 16-byte aligned) is scratch for b in pivot order.
 template <int RPL, int R>
-__device__ void lu32_solve(const float *A, int p32, int M, const int *step, const int *perm,
-                           float (&z)[RPL][R], float *X) {
+__device__ void gj32_apply(const float *S, int p32, int M, const int *step, const int *perm, float *V,
+                           float *Bp) {
     const int lane = threadIdx.x & 31;
-    for (int kk = 0; kk < M; ++kk) {
-        const int p = perm[kk], owner = p & 31, qp = p >> 5;
-        float y[R];
+    const int C4 = (M + 3) >> 2;
+    for (int e = lane; e < 4 * C4 * R; e += 32) {
+        const int k = e / R, c = e - k * R;
+        Bp[e] = k < M ? V[perm[k] * R + c] : 0.0f;
+    }
+    __syncwarp();
+    float y[RPL][R];
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            float v = z[0][c];
+    for (int q = 0; q < RPL; ++q)
 #pragma unroll
-            for (int q = 1; q < RPL; ++q)
-                if (qp == q) v = z[q][c];
-            y[c] = __shfl_sync(kFull, v, owner);
+        for (int c = 0; c < R; ++c) y[q][c] = 0.0f;
+    const float4 *B4 = reinterpret_cast<const float4 *>(Bp);
+    for (int c4 = 0; c4 < C4; ++c4) {
+        float b[4 * R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const float4 v = B4[c4 * R + t];
+            b[4 * t] = v.x; b[4 * t + 1] = v.y; b[4 * t + 2] = v.z; b[4 * t + 3] = v.w;
         }
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
-            if (step[q] > kk) {
-                const float a = A[(lane + 32 * q) * p32 + kk];
+            if (lane + 32 * q < M) {
+                const float4 sv = reinterpret_cast<const float4 *>(S + (lane + 32 * q) * p32)[c4];
 #pragma unroll
-                for (int c = 0; c < R; ++c) z[q][c] = fmaf(-a, y[c], z[q][c]);
+                for (int c = 0; c < R; ++c) {
+                    float acc = y[q][c];
+                    acc = fmaf(sv.x, b[c], acc);
+                    acc = fmaf(sv.y, b[R + c], acc);
+                    acc = fmaf(sv.z, b[2 * R + c], acc);
+                    acc = fmaf(sv.w, b[3 * R + c], acc);
+                    y[q][c] = acc;
+                }
             }
     }
-    for (int kk = M - 1; kk >= 0; --kk) {
-        const int p = perm[kk], owner = p & 31, qp = p >> 5;
-        const float ip = A[p * p32 + kk];
-        float xk[R];
+    __syncwarp();
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            float v = z[0][c];
+    for (int q = 0; q < RPL; ++q)
+        if (lane + 32 * q < M)
 #pragma unroll
-            for (int q = 1; q < RPL; ++q)
-                if (qp == q) v = z[q][c];
-            xk[c] = __shfl_sync(kFull, v, owner) * ip;
-        }
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-            if (step[q] >= 0 && step[q] < kk) {
-                const float a = A[(lane + 32 * q) * p32 + kk];
-#pragma unroll
-                for (int c = 0; c < R; ++c) z[q][c] = fmaf(-a, xk[c], z[q][c]);
-            }
-        if (lane == 0)
-#pragma unroll
-            for (int c = 0; c < R; ++c) X[kk * R + c] = xk[c];
-    }
+            for (int c = 0; c < R; ++c) V[step[q] * R + c] = y[q][c];
     __syncwarp();
 }
 
 // Per-warp shared memory of the mixed kernel (byte offsets, 16-aligned).
 struct MixedLayout {
     int pA, p32;
-    size_t a64, q64, b64, x64, xi, a32, u32, v32, perm, bytes;
+    size_t a64, q64, b64, x64, xi, a32, u32, v32, bp, perm, bytes;
 };
 
 __host__ __device__ inline MixedLayout mixed_layout(int n_max, int l, int R, int dim) {
     MixedLayout L{};
-    const int M = n_max + l;
+    const int M = n_max + l, C4 = (M + 3) / 4;
     L.pA = n_max | 1;
-    L.p32 = ((M + 1) & ~1) | 2;        // 2 * odd: float2 rows, few column conflicts
-    if (L.p32 < M) L.p32 += 4;
+    L.p32 = 4 * (C4 | 1);              // 4 * odd >= 4 * ceil(M/4)
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -489,301 +607,357 @@ __host__ __device__ inline MixedLayout mixed_layout(int n_max, int l, int R, int
     L.x64 = take((size_t)M * R * 8);
     L.xi = take((size_t)n_max * dim * 8);
     L.a32 = take((size_t)M * L.p32 * 4);
-    L.u32 = take((size_t)L.p32 * 4);
-    L.v32 = take((size_t)M * (R + 1) * 4);
+    L.u32 = take((size_t)2 * 4 * C4 * 4);
+    L.v32 = take((size_t)M * R * 4);
+    L.bp = take((size_t)4 * C4 * R * 4);
     L.perm = take((size_t)M * 4);
     L.bytes = o;
     return L;
 }
 
-// Compact FP64 system for the residuals: A64 [n x pA] (diagonal 0), Q64
-// [n x l], B64 [M x R] (rows < n: l_phi, rows n + b: l_q).  Returns max |K|.
+// ------------------------------------------------ double-FP32 arithmetic
+// A value is the unevaluated sum hi + lo of two floats (float2 {hi, lo},
+// |lo| <= ulp(hi)), about 48 significant bits, computed on the FP32 pipe
+// (GB300 issues FP32 at ~70x its FP64 rate).  Built from the error-free
+// transformations TwoSum (Knuth), Fast2Sum (Dekker) and the FMA-based exact
+// product; the _rn intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// |a| >= |b| or a == 0
+__device__ __forceinline__ float2 ff_fast_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float2 t = ff_two_sum(a.x, b.x);
+    return ff_fast_sum(t.x, __fadd_rn(t.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    return ff_fast_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_scale(float2 a, float b) {
+    const float p = __fmul_rn(a.x, b);
+    return ff_fast_sum(p, fmaf(a.y, b, fmaf(a.x, b, -p)));
+}
+// square root by one Newton correction of the FP32 root: (a - h^2) / (2h)
+__device__ __forceinline__ float2 ff_sqrt(float2 a) {
+    if (!(a.x > 0.0f)) return make_float2(0.0f, 0.0f);
+    const float h = __fsqrt_rn(a.x);
+    const float p = __fmul_rn(h, h);
+    const float t = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), fmaf(h, h, -p)), a.y);
+    return ff_fast_sum(h, __fmul_rn(t, __fmul_rn(0.5f, __frcp_rn(h))));
+}
+__device__ __forceinline__ float2 ff_from_double(double d) {
+    const float h = __double2float_rn(d);
+    return make_float2(h, __double2float_rn(d - (double)h));
+}
+// r^k for odd k >= 1 from r^2
+__device__ __forceinline__ float2 ff_phs(float2 r2, int k) {
+    float2 v = ff_sqrt(r2);
+    for (int i = 1; i < k; i += 2) v = ff_mul(v, r2);
+    return v;
+}
+// r^(k-2) for odd k >= 3 from r^2
+__device__ __forceinline__ float2 ff_phs_km2(float2 r2, int k) {
+    float2 v = ff_sqrt(r2);
+    for (int i = 3; i < k; i += 2) v = ff_mul(v, r2);
+    return v;
+}
+
+// The system for the residuals in double-FP32: A [n x pA] (diagonal 0), Q
+// [n x l], B [M x R] (rows < n: l_phi, rows n + b: l_q), from the scaled
+// offsets xf [n x DIM] (double-FP32).  Returns max |K| over A and Q (FP32).
 template <int DIM>
-__device__ double assemble_mixed(const WParams &P, int64_t row, int n, const double *xi,
-                                 double *A64, int pA, double *Q64, double *B64, int R) {
+__device__ float assemble_ff(const WParams &P, int64_t row, int n, const float2 *xf, float2 *A, int pA,
+                             float2 *Q, float2 *B, int R) {
     const int lane = threadIdx.x & 31;
     const int l = P.l, k = P.k, di = DIM - 2;
-    double amax = 0.0;
+    float amax = 0.0f;
     for (int d = 1; d <= n / 2; ++d) {
         const int cnt = (2 * d == n) ? n / 2 : n;
         for (int r = lane; r < cnt; r += 32) {
             int c = r + d;
             if (c >= n) c -= n;
-            double r2 = 0.0;
+            float2 r2 = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
-                const double t = xi[r * DIM + a] - xi[c * DIM + a];
-                r2 = fma(t, t, r2);
+                const float2 t = ff_sub(xf[r * DIM + a], xf[c * DIM + a]);
+                r2 = ff_add(r2, ff_mul(t, t));
             }
-            const double v = phs(r2, k);
-            A64[r * pA + c] = v;
-            A64[c * pA + r] = v;
-            amax = fmax(amax, v);
+            const float2 v = ff_phs(r2, k);
+            A[r * pA + c] = v;
+            A[c * pA + r] = v;
+            amax = fmaxf(amax, v.x);
         }
     }
     for (int r = lane; r < n; r += 32) {
-        A64[r * pA + r] = 0.0;
-        double *Qr = Q64 + r * l;
-        Qr[0] = 1.0;
+        A[r * pA + r] = make_float2(0.0f, 0.0f);
+        float2 *Qr = Q + r * l;
+        Qr[0] = make_float2(1.0f, 0.0f);
         for (int b = 1; b < l; ++b) {
-            const double v = Qr[c_mono.parent[di][b]] * xi[r * DIM + c_mono.var[di][b]];
+            const float2 v = ff_mul(Qr[c_mono.parent[di][b]], xf[r * DIM + c_mono.var[di][b]]);
             Qr[b] = v;
-            amax = fmax(amax, fabs(v));
+            amax = fmaxf(amax, fabsf(v.x));
         }
-        double r2 = 0.0;
+        float2 r2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) r2 = fma(xi[r * DIM + a], xi[r * DIM + a], r2);
-        double rk2 = sqrt(r2);
-        for (int i = 3; i < k; i += 2) rk2 *= r2;
+        for (int a = 0; a < DIM; ++a) r2 = ff_add(r2, ff_mul(xf[r * DIM + a], xf[r * DIM + a]));
+        const float2 rk2 = ff_phs_km2(r2, k);
         for (int cI = 0; cI < R; ++cI) {
             const int op = P.opcode[cI];
-            double v;
+            float2 v;
             if (cI >= P.R) {
-                v = 0.0;                  // unused solver column
+                v = make_float2(0.0f, 0.0f);      // unused solver column
             } else if (op == 0) {
-                v = (double)(k * (k + DIM - 2)) * rk2;
+                v = ff_scale(rk2, (float)(k * (k + DIM - 2)));
             } else {
-                double dot;
+                float2 dot;
                 if (op == 4) {
-                    dot = 0.0;
+                    dot = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int a = 0; a < DIM; ++a) dot = fma(P.normals[row * DIM + a], xi[r * DIM + a], dot);
+                    for (int a = 0; a < DIM; ++a)
+                        dot = ff_add(dot, ff_mul(ff_from_double(P.normals[row * DIM + a]), xf[r * DIM + a]));
                 } else {
-                    dot = xi[r * DIM + (op - 1)];
+                    dot = xf[r * DIM + (op - 1)];
                 }
-                v = -(double)k * rk2 * dot;
+                v = ff_scale(ff_mul(rk2, dot), -(float)k);
             }
-            B64[r * R + cI] = v;
+            B[r * R + cI] = v;
         }
     }
     for (int b = lane; b < l; b += 32) {
         for (int cI = 0; cI < R; ++cI) {
             const int op = P.opcode[cI];
-            double v = 0.0;
-            if (cI >= P.R) {
-                v = 0.0;
-            } else if (op == 0) {
-                v = (double)c_mono.lap[di][b];
-            } else {
-                const int a = c_mono.lin[di][b];
-                if (a >= 0) v = op == 4 ? P.normals[row * DIM + a] : ((a == op - 1) ? 1.0 : 0.0);
+            float2 v = make_float2(0.0f, 0.0f);
+            if (cI < P.R) {
+                if (op == 0) {
+                    v.x = (float)c_mono.lap[di][b];
+                } else {
+                    const int a = c_mono.lin[di][b];
+                    if (a >= 0) v = op == 4 ? ff_from_double(P.normals[row * DIM + a])
+                                            : make_float2((a == op - 1) ? 1.0f : 0.0f, 0.0f);
+                }
             }
-            B64[(n + b) * R + cI] = v;
+            B[(n + b) * R + cI] = v;
         }
     }
     __syncwarp();
-    return warp_max(fmax(amax, 1.0));
+    return warp_maxf(fmaxf(amax, 1.0f));
 }
 
-// One stencil (row) with the FP32 + FP64-refinement solver; `base` is the
-// warp's shared memory.  Returns true if the row must go to the FP64 solver
-// (its status is then MM_ST_NONCONVERGED and its weights are not written).
+// Compensated dot product (Ogita, Rump & Oishi) in double-FP32: acc -= kx * xx.
+// The product of the high parts is split exactly and subtracted from hi with
+// TwoSum; the rounding errors go to lo and the cross terms to la and lb (three
+// independent chains, so consecutive terms overlap).  The value is
+// hi + (lo + (la + lb)).
+struct FFAcc {
+    float hi, lo, la, lb;
+    __device__ __forceinline__ explicit FFAcc(float2 b) : hi(b.x), lo(b.y), la(0.0f), lb(0.0f) {}
+    __device__ __forceinline__ void sub(float2 kx, float2 xx) {
+        const float p = __fmul_rn(kx.x, xx.x);
+        const float pe = fmaf(kx.x, xx.x, -p);
+        const float2 t = ff_two_sum(hi, -p);
+        hi = t.x;
+        lo = __fadd_rn(lo, __fsub_rn(t.y, pe));
+        la = fmaf(-kx.x, xx.y, la);
+        lb = fmaf(-kx.y, xx.x, lb);
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(hi, __fadd_rn(lo, __fadd_rn(la, lb))); }
+};
+
+// One stencil (row) with the FP32 + refinement solver; `base` is the warp's
+// shared memory.  Returns true if the row must go to the FP64 solver (its
+// status is then MM_ST_NONCONVERGED and its weights are not written).
+//
+// K is inverted once in FP32 (Gauss-Jordan above); every solve is then a
+// product with that inverse.  The 1-norm condition number of K follows from
+// ||K||_1 and the exact infinity norm of the computed inverse (K is
+// symmetric, so both norms agree); a stencil with ||K|| ||K^-1|| u32 above
+// the bound goes to the FP64 solver.  Refinement: x <- x + K^-1 (b - K x),
+// with K, b and x held in double-FP32 and the residual accumulated by a
+// compensated dot product, for at least two steps and until the observed
+// contraction shows the remaining error below the tolerance.  A last
+// correction from the constraint rows alone makes the monomials hold to the
+// residual's precision rather than to the refinement tolerance.
 template <int DIM, int RPL, int R>
 __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base) {
     const int lane = threadIdx.x & 31;
     const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
-    double *A64 = (double *)(base + Ly.a64);
-    double *Q64 = (double *)(base + Ly.q64);
-    double *B64 = (double *)(base + Ly.b64);
-    double *X64 = (double *)(base + Ly.x64);
+    float2 *Af = (float2 *)(base + Ly.a64);
+    float2 *Qf = (float2 *)(base + Ly.q64);
+    float2 *Bf = (float2 *)(base + Ly.b64);
+    float2 *Xf = (float2 *)(base + Ly.x64);
     double *xi = (double *)(base + Ly.xi);
-    float *A32 = (float *)(base + Ly.a32);
+    float *S = (float *)(base + Ly.a32);
     float *U32 = (float *)(base + Ly.u32);
     float *V32 = (float *)(base + Ly.v32);
+    float *Bp = (float *)(base + Ly.bp);
     int *perm = (int *)(base + Ly.perm);
     const int pA = Ly.pA, p32 = Ly.p32, l = P.l;
     const float u32 = FLT_EPSILON * 0.5f;
-    {
-        int n;
-        int64_t rb;
-        double s;
-        if (!load_stencil<DIM>(P, row, n, rb, xi, s)) {
-            reject_row(P, row, rb, n, MM_ST_BADARG);
-            __syncwarp();
-            return false;
-        }
-        const int M = n + l;
-        const double amax = assemble_mixed<DIM>(P, row, n, xi, A64, pA, Q64, B64, R);
-        // FP32 system: the A block as fl32 of the FP64 one, Q and Q^T from the
-        // FP32 offsets (own rows; Q^T entries written by the row's owner)
-        int step[RPL];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            const int r = lane + 32 * q;
-            step[q] = r < M ? kBig : -1;
-            if (r < n) {
-                float *Ar = A32 + r * p32;
-                for (int c = 0; c < n; ++c) Ar[c] = (float)A64[r * pA + c];
-                float x32[DIM];
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) x32[d] = (float)xi[r * DIM + d];
-                float *Qr = Ar + n;
-                Qr[0] = 1.0f;
-                A32[n * p32 + r] = 1.0f;
-                for (int b = 1; b < l; ++b) {
-                    const float v = Qr[c_mono.parent[DIM - 2][b]] * x32[c_mono.var[DIM - 2][b]];
-                    Qr[b] = v;
-                    A32[(n + b) * p32 + r] = v;
-                }
-            } else if (r < M) {
-                for (int c = n; c < M; ++c) A32[r * p32 + c] = 0.0f;
-            }
-        }
+    int n;
+    int64_t rb;
+    double s;
+    if (!load_stencil<DIM>(P, row, n, rb, xi, s)) {
+        reject_row(P, row, rb, n, MM_ST_BADARG);
         __syncwarp();
-        float n1 = 0.0f;   // ||K||_1 = max row sum (symmetric)
+        return false;
+    }
+    const int M = n + l, W4 = 4 * ((M + 3) >> 2);
+    // scaled offsets to double-FP32, in place (same 8 bytes per coordinate)
+    float2 *xf = reinterpret_cast<float2 *>(xi);
+    for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
+    __syncwarp();
+    const float amax = assemble_ff<DIM>(P, row, n, xf, Af, pA, Qf, Bf, R);
+    // FP32 system: the high parts (own rows; Q^T entries written by the row's owner)
+    int step[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+        step[q] = r < M ? kBig : -1;
+        if (r < n) {
+            float *Sr = S + r * p32;
+            for (int c = 0; c < n; ++c) Sr[c] = Af[r * pA + c].x;
+            for (int b = 0; b < l; ++b) {
+                const float v = Qf[r * l + b].x;
+                Sr[n + b] = v;
+                S[(n + b) * p32 + r] = v;
+            }
+        } else if (r < M) {
+            for (int c = n; c < M; ++c) S[r * p32 + c] = 0.0f;
+        }
+        if (r < M)
+            for (int c = M; c < W4; ++c) S[r * p32 + c] = 0.0f;
+    }
+    __syncwarp();
+    float n1 = 0.0f;   // ||K||_1 = max row sum (symmetric)
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+        if (r < M) {
+            float rs = 0.0f;
+            for (int c = 0; c < M; ++c) rs += fabsf(S[r * p32 + c]);
+            n1 = fmaxf(n1, rs);
+        }
+    }
+    n1 = warp_maxf(n1);
+    bool queue = !gj32_invert<RPL>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
+    if (!queue) {
+        float ninv = 0.0f;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             const int r = lane + 32 * q;
             if (r < M) {
                 float rs = 0.0f;
-                for (int c = 0; c < M; ++c) rs += fabsf(A32[r * p32 + c]);
-                n1 = fmaxf(n1, rs);
+                for (int c = 0; c < M; ++c) rs += fabsf(S[r * p32 + c]);
+                ninv = fmaxf(ninv, rs);
             }
         }
-        n1 = warp_maxf(n1);
-        bool queue = !lu32_implicit<RPL>(A32, p32, M, step, perm, U32, (float)M * u32 * (float)amax);
-        bool conv = false;
-        if (!queue) {
-            // Refinement.  The first two solves carry one extra column: a step of
-            // Hager's 1-norm estimator of K^-1 (y = K^-1 e/M, then z = K^-T sign(y),
-            // est = max(||y||_1, ||z||_inf); K is symmetric), which gates the
-            // stencil to the FP64 solve if est * ||K||_1 * u32 is too large.
-            constexpr int RC = R + 1;
-            float z[RPL][RC];
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-                const int r = lane + 32 * q;
-#pragma unroll
-                for (int c = 0; c < R; ++c) z[q][c] = r < M ? (float)B64[r * R + c] : 0.0f;
-                z[q][R] = r < M ? 1.0f / M : 0.0f;
-            }
-            lu32_solve<RPL, RC>(A32, p32, M, step, perm, z, V32);
-            float est = 0.0f;
-            double dmax = 0.0;
-            for (int i = lane; i < M; i += 32) {
-                est += fabsf(V32[i * RC + R]);
-#pragma unroll
-                for (int c = 0; c < R; ++c) {
-                    const double d = (double)V32[i * RC + c];
-                    X64[i * R + c] = d;
-                    dmax = fmax(dmax, fabs(d));
-                }
-            }
-            est = warp_sumf(est);
-            double dprev = warp_max(dmax);
-            float sg[RPL];
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-                const int r = lane + 32 * q;
-                sg[q] = r < M ? (V32[r * RC + R] >= 0.0f ? 1.0f : -1.0f) : 0.0f;
-            }
-            __syncwarp();
-            for (int it = 1; it <= P.ir_max_steps; ++it) {
-                // FP64 residual b - K64 x over the nonzero blocks
-                for (int e = lane; e < M * R; e += 32) {
-                    const int i = e / R, c = e - i * R;
-                    double acc = B64[e];
-                    if (i < n) {
-                        const double *Ai = A64 + i * pA;
-                        const double *Qi = Q64 + i * l;
-                        for (int j = 0; j < n; ++j) acc = fma(-Ai[j], X64[j * R + c], acc);
-                        for (int b = 0; b < l; ++b) acc = fma(-Qi[b], X64[(n + b) * R + c], acc);
-                    } else {
-                        const int b = i - n;
-                        for (int j = 0; j < n; ++j) acc = fma(-Q64[j * l + b], X64[j * R + c], acc);
-                    }
-                    V32[e] = (float)acc;
-                }
-                __syncwarp();
-                double dmx = 0.0, xmax = 0.0;
-                if (it == 1) {
-#pragma unroll
-                    for (int q = 0; q < RPL; ++q) {
-                        const int r = lane + 32 * q;
-#pragma unroll
-                        for (int c = 0; c < R; ++c) z[q][c] = r < M ? V32[r * R + c] : 0.0f;
-                        z[q][R] = sg[q];
-                    }
-                    __syncwarp();
-                    lu32_solve<RPL, RC>(A32, p32, M, step, perm, z, V32);
-                    float zinf = 0.0f;
-                    for (int i = lane; i < M; i += 32) {
-                        zinf = fmaxf(zinf, fabsf(V32[i * RC + R]));
-#pragma unroll
-                        for (int c = 0; c < R; ++c) {
-                            const double d = (double)V32[i * RC + c];
-                            const double xn = X64[i * R + c] + d;
-                            X64[i * R + c] = xn;
-                            dmx = fmax(dmx, fabs(d));
-                            if (i < n) xmax = fmax(xmax, fabs(xn));
-                        }
-                    }
-                    zinf = warp_maxf(zinf);
-                    const float kest = n1 * fmaxf(est, zinf);
-                    if (!((double)kest * u32 <= P.kappa_max)) { queue = true; break; }
-                } else {
-                    float zr[RPL][R];
-#pragma unroll
-                    for (int q = 0; q < RPL; ++q) {
-                        const int r = lane + 32 * q;
-#pragma unroll
-                        for (int c = 0; c < R; ++c) zr[q][c] = r < M ? V32[r * R + c] : 0.0f;
-                    }
-                    __syncwarp();
-                    lu32_solve<RPL, R>(A32, p32, M, step, perm, zr, V32);
-                    for (int e = lane; e < M * R; e += 32) {
-                        const double d = (double)V32[e];
-                        const double xn = X64[e] + d;
-                        X64[e] = xn;
-                        dmx = fmax(dmx, fabs(d));
-                        if (e < n * R) xmax = fmax(xmax, fabs(xn));
-                    }
-                }
-                dmx = warp_max(dmx);
-                xmax = warp_max(xmax);
-                // the observed contraction of the last step bounds the error left
-                const double theta = dmx / fmax(dprev, 1e-300);
-                if (theta < 0.5 && theta / (1.0 - theta) * dmx <= P.ir_tol * xmax) {
-                    conv = true;
-                    break;
-                }
-                dprev = dmx;
-                __syncwarp();
-            }
-            if (conv) {
-                // Constraint rows Q^T w = l_q: one more FP64 residual on those rows
-                // only, corrected through the FP32 factors, so the monomials are
-                // reproduced to FP64 rounding rather than to the refinement tolerance.
-                __syncwarp();
-                for (int e = lane; e < l * R; e += 32) {
-                    const int b = e / R, c = e - b * R;
-                    double acc = B64[(n + b) * R + c];
-                    for (int j = 0; j < n; ++j) acc = fma(-Q64[j * l + b], X64[j * R + c], acc);
-                    V32[e] = (float)acc;
-                }
-                __syncwarp();
-                float zr[RPL][R];
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const int r = lane + 32 * q;
-#pragma unroll
-                    for (int c = 0; c < R; ++c) zr[q][c] = (r >= n && r < M) ? V32[(r - n) * R + c] : 0.0f;
-                }
-                __syncwarp();
-                lu32_solve<RPL, R>(A32, p32, M, step, perm, zr, V32);
-                for (int e = lane; e < n * R; e += 32) X64[e] += (double)V32[e];
-                __syncwarp();
-            }
-        }
-        if (!conv) {
-            if (P.status && lane == 0) P.status[row] = MM_ST_NONCONVERGED;
-            __syncwarp();
-            return true;
-        }
-        store_weights(P, rb, n, s, X64, R, 0);
-        if (P.status && lane == 0) P.status[row] = MM_ST_OK;
-        __syncwarp();
+        ninv = warp_maxf(ninv);
+        queue = !((double)n1 * (double)ninv * u32 <= P.kappa_max);
     }
+    bool conv = false;
+    if (!queue) {
+        for (int e = lane; e < M * R; e += 32) V32[e] = Bf[e].x;
+        __syncwarp();
+        gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
+        float dmax = 0.0f;
+        for (int e = lane; e < M * R; e += 32) {
+            const float d = V32[e];
+            Xf[e] = make_float2(d, 0.0f);
+            dmax = fmaxf(dmax, fabsf(d));
+        }
+        float dprev = warp_maxf(dmax);
+        __syncwarp();
+        for (int it = 1; it <= P.ir_max_steps; ++it) {
+            // residual b - K x over the nonzero blocks
+            for (int e = lane; e < M * R; e += 32) {
+                const int i = e / R, c = e - i * R;
+                FFAcc acc(Bf[e]);
+                if (i < n) {
+                    const float2 *Ai = Af + i * pA;
+                    const float2 *Qi = Qf + i * l;
+                    for (int j = 0; j < n; ++j) acc.sub(Ai[j], Xf[j * R + c]);
+                    for (int b = 0; b < l; ++b) acc.sub(Qi[b], Xf[(n + b) * R + c]);
+                } else {
+                    const int b = i - n;
+                    for (int j = 0; j < n; ++j) acc.sub(Qf[j * l + b], Xf[j * R + c]);
+                }
+                V32[e] = acc.value();
+            }
+            __syncwarp();
+            gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
+            float dmx = 0.0f, xmax = 0.0f;
+            for (int e = lane; e < M * R; e += 32) {
+                const float d = V32[e];
+                const float2 x = Xf[e];
+                const float2 t = ff_two_sum(x.x, d);
+                const float2 xn = ff_fast_sum(t.x, __fadd_rn(t.y, x.y));
+                Xf[e] = xn;
+                dmx = fmaxf(dmx, fabsf(d));
+                if (e < n * R) xmax = fmaxf(xmax, fabsf(xn.x));
+            }
+            dmx = warp_maxf(dmx);
+            xmax = warp_maxf(xmax);
+            // the observed contraction of the last step bounds the error left;
+            // it is taken from two corrections (the first step's ratio compares
+            // a correction with the solution itself and can underestimate it)
+            const float theta = dmx / fmaxf(dprev, 1e-30f);
+            if (it >= 2 && theta < 0.5f && theta / (1.0f - theta) * dmx <= (float)P.ir_tol * xmax) {
+                conv = true;
+                break;
+            }
+            dprev = dmx;
+            __syncwarp();
+        }
+        if (conv) {
+            __syncwarp();
+            for (int e = lane; e < M * R; e += 32) {
+                const int i = e / R, c = e - i * R;
+                float r = 0.0f;
+                if (i >= n) {
+                    const int b = i - n;
+                    FFAcc acc(Bf[e]);
+                    for (int j = 0; j < n; ++j) acc.sub(Qf[j * l + b], Xf[j * R + c]);
+                    r = acc.value();
+                }
+                V32[e] = r;
+            }
+            __syncwarp();
+            gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
+            for (int e = lane; e < n * R; e += 32) {
+                const float2 x = Xf[e];
+                const float2 t = ff_two_sum(x.x, V32[e]);
+                Xf[e] = ff_fast_sum(t.x, __fadd_rn(t.y, x.y));
+            }
+            __syncwarp();
+        }
+    }
+    if (!conv) {
+        if (P.status && lane == 0) P.status[row] = MM_ST_NONCONVERGED;
+        __syncwarp();
+        return true;
+    }
+    // unscaled store
+    const double inv_s = 1.0 / s;
+    for (int cI = 0; cI < P.R; ++cI) {
+        const double sc = P.opcode[cI] == 0 ? inv_s * inv_s : inv_s;
+        double *out = P.vals[cI] + rb;
+        for (int j = lane; j < n; j += 32) {
+            const float2 x = Xf[j * R + cI];
+            out[j] = ((double)x.x + (double)x.y) * sc;
+        }
+    }
+    if (P.status && lane == 0) P.status[row] = MM_ST_OK;
+    __syncwarp();
     return false;
 }
 
