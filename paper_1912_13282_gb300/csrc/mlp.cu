@@ -429,13 +429,17 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
 }
 
 // ------------------------------------------------- projection and residual check
-// One warp per stencil (n <= 32, l <= 32).  wt: predicted scaled Laplacian
-// weights [n] (FP32).  Least-norm correction onto Q^T w = l_q:
-//     w = wt + Q z,  (Q^T Q) z = l_q - Q^T wt,
-// solved with an FP32 Cholesky of the Jacobi-scaled Gram matrix and FP64
-// constraint residuals (up to 4 passes, until the rows hold to 1e-15 relative).
-// Residual check: r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least squares),
-// rho = ||r - Q lambda||_inf / ||l_phi||_inf; accept if rho <= tau (FP32).
+// One warp per stencil (n <= 32, l <= 16).  wt: predicted scaled Laplacian
+// weights [n] (FP32).  Least-norm correction onto the monomial rows
+// Q^T w = l_q of the augmented system:
+//     w = wt + Q z,  (Q^T Q) z = l_q - Q^T w,
+// repeated while the constraint rows are off by more than 1e-13 of their
+// terms (at most 6 passes).  Q, w and the constraint residuals are carried in
+// double-FP32 (compensated sums on the FP32 pipe); z comes from an FP32
+// inverse of the Jacobi-scaled Gram matrix (in-place Gauss-Jordan, no
+// pivoting: the matrix is symmetric positive definite).
+// Residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least
+// squares), rho = ||r - Q lambda||_inf / ||l_phi||_inf; accept if rho <= tau.
 struct ProjParams {
     WParams P;              // LAP only, k, m, row range, output vals[0]
     const float *wt;        // [rows x n] predictions (scaled units), row - row_begin
@@ -444,161 +448,185 @@ struct ProjParams {
     float *rho_out;         // optional [rows]
 };
 
+__device__ __forceinline__ float phs32(float r2, int k) {
+    float p = sqrtf(r2);
+    for (int i = 1; i < k; i += 2) p *= r2;
+    return p;
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjParams J) {
-    constexpr int NM = 32, LM = 16;
+    constexpr int NM = 32, LM = 16, QP = LM + 1, GP = LM + 4;
     const WParams &P = J.P;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    __shared__ double s_xi[4][NM * DIM];
-    __shared__ float s_xi32[4][NM * DIM];
-    __shared__ double s_Q[4][NM][LM + 1];
-    __shared__ float s_Q32[4][NM][LM + 1];
-    __shared__ float s_G[4][LM][2 * LM + 1];    // [D G D | I] -> [I | (D G D)^-1]
-    __shared__ double s_w[4][NM];
-    __shared__ float s_w32[4][NM], s_r[4][NM];
-    __shared__ float s_z[4][LM], s_d[4][LM], s_m[4][LM];
-    double *xi = s_xi[wib];
-    float *x32 = s_xi32[wib];
-    float (*G)[2 * LM + 1] = s_G[wib];
+    __shared__ double s_xi[4][NM * DIM];          // offsets (FP64, then double-FP32 in place)
+    __shared__ float2 s_Q[4][NM][QP];             // Q (double-FP32)
+    __shared__ __align__(16) float s_G[4][LM][GP]; // Jacobi-scaled Gram matrix, then its inverse
+    __shared__ float s_A[4][NM][NM + 1];          // FP32 phi matrix for the residual check
+    __shared__ float2 s_w[4][NM];                 // weights (double-FP32)
+    __shared__ float s_u[4][LM], s_d[4][LM], s_z[4][LM], s_r[4][NM];
+    float2 (*Q)[QP] = s_Q[wib];
+    float (*G)[GP] = s_G[wib];
+    float (*A)[NM + 1] = s_A[wib];
+    float2 *w = s_w[wib];
+    float *u = s_u[wib], *dsc = s_d[wib], *zz = s_z[wib], *rr = s_r[wib];
     const int l = P.l, di = DIM - 2, k = P.k;
+    const int bl = lane & 15, hl = lane >> 4;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t row = P.row_begin + gw; row < P.row_end; row += nw) {
         int n;
         int64_t rb;
         double s;
+        double *xi = s_xi[wib];
         if (!load_stencil<DIM>(P, row, n, rb, xi, s) || n > NM || l > LM) {
             reject_row(P, row, rb, n, MM_ST_BADARG);
             __syncwarp();
             continue;
         }
-        // Q by stencil node (FP64 and FP32), predicted weights
+        float2 *xf = reinterpret_cast<float2 *>(xi);
+        for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
+        __syncwarp();
+        // Q by stencil node, predicted weights
         if (lane < n) {
-            double *Qj = s_Q[wib][lane];
-            float *Qf = s_Q32[wib][lane];
-            Qj[0] = 1.0;
-            Qf[0] = 1.0f;
-            for (int b = 1; b < l; ++b) {
-                const double v = Qj[c_mono.parent[di][b]] * xi[lane * DIM + c_mono.var[di][b]];
-                Qj[b] = v;
-                Qf[b] = (float)v;
+            float2 *Qj = Q[lane];
+            Qj[0] = make_float2(1.0f, 0.0f);
+            for (int b = 1; b < l; ++b) Qj[b] = ff_mul(Qj[c_mono.parent[di][b]], xf[lane * DIM + c_mono.var[di][b]]);
+            w[lane] = make_float2(J.wt[(row - P.row_begin) * n + lane], 0.0f);
+        }
+        // FP32 phi matrix: unordered pairs (r, (r + d) mod n), each once
+        for (int d = 1; d <= n / 2; ++d) {
+            const int cnt = (2 * d == n) ? n / 2 : n;
+            for (int r = lane; r < cnt; r += 32) {
+                int c = r + d;
+                if (c >= n) c -= n;
+                float r2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    const float t = xf[r * DIM + a].x - xf[c * DIM + a].x;
+                    r2 = fmaf(t, t, r2);
+                }
+                const float v = phs32(r2, k);
+                A[r][c] = v;
+                A[c][r] = v;
             }
-            for (int a = 0; a < DIM; ++a) x32[lane * DIM + a] = (float)xi[lane * DIM + a];
-            s_w[wib][lane] = (double)J.wt[(row - P.row_begin) * n + lane];
         }
+        if (lane < n) A[lane][lane] = 0.0f;
         __syncwarp();
-        // Gram matrix Q^T Q (FP32) with Jacobi scaling D = diag^-1/2, and its
-        // inverse by Gauss-Jordan on [D G D | I] (symmetric positive definite:
-        // no pivoting)
-        for (int e = lane; e < l * l; e += 32) {
-            const int a = e / l, b = e % l;
-            float acc = 0.f;
-            for (int j = 0; j < n; ++j) acc = fmaf(s_Q32[wib][j][a], s_Q32[wib][j][b], acc);
+        // Gram matrix Q^T Q (FP32, upper triangle), Jacobi scaling
+        for (int e = lane; e < l * (l + 1) / 2; e += 32) {
+            int a = 0, t = e;
+            while (t >= l - a) { t -= l - a; ++a; }
+            const int b = a + t;
+            float acc = 0.0f;
+            for (int j = 0; j < n; ++j) acc = fmaf(Q[j][a].x, Q[j][b].x, acc);
             G[a][b] = acc;
-            G[a][l + b] = a == b ? 1.f : 0.f;
+            G[b][a] = acc;
         }
         __syncwarp();
-        if (lane < l) s_d[wib][lane] = rsqrtf(fmaxf(G[lane][lane], 1e-30f));
+        if (lane < l) dsc[lane] = rsqrtf(fmaxf(G[lane][lane], 1e-30f));
         __syncwarp();
         for (int e = lane; e < l * l; e += 32) {
-            const int a = e / l, b = e % l;
-            G[a][b] *= s_d[wib][a] * s_d[wib][b];
+            const int a = e / l, b = e - a * l;
+            G[a][b] *= dsc[a] * dsc[b];
         }
         __syncwarp();
+        // in-place Gauss-Jordan inverse; lanes (row bl, column half hl)
         bool ok = true;
+        const int c0 = 8 * hl, c1 = min(l, c0 + 8);
         for (int c = 0; c < l; ++c) {
             const float piv = G[c][c];
-            ok &= piv > 0.f;
-            const float ip = piv > 0.f ? 1.f / piv : 0.f;
+            ok &= piv > 0.0f;
+            const float ip = piv > 0.0f ? __frcp_rn(piv) : 0.0f;
+            const bool live = bl < l && bl != c;
+            const float m = live ? G[bl][c] : 0.0f;
             __syncwarp();
-            for (int e = lane; e < 2 * l; e += 32) G[c][e] *= ip;
-            if (lane < l) s_m[wib][lane] = G[lane][c];     // multipliers, read before the update
+            if (lane < l) {
+                const float v = G[c][lane] * ip;
+                u[lane] = lane == c ? 0.0f : v;
+                G[c][lane] = lane == c ? ip : v;
+            }
             __syncwarp();
-            for (int e = lane; e < l * 2 * l; e += 32) {
-                const int i = e / (2 * l), j = e % (2 * l);
-                if (i != c) G[i][j] = fmaf(-s_m[wib][i], G[c][j], G[i][j]);
+            if (live) {
+                for (int j = c0; j < c1; ++j) G[bl][j] = fmaf(-m, u[j], G[bl][j]);
+                if (c >= c0 && c < c1) G[bl][c] = -m * ip;
             }
             __syncwarp();
         }
-        // Correction passes: FP64 constraint residual c = l_q - Q^T w (all
-        // lanes: lane = b + 16 h sums half h of the nodes), z = D Ginv D c in
-        // FP32, w += Q z in FP64 (so w - wt stays in range(Q)).
-        const int bl = lane & 15, hl = lane >> 4, jh = (n + 1) / 2;
-        for (int pass = 0; pass < 5; ++pass) {
-            double cb = 0.0, sc = 0.0;
-            if (bl < l)
-                for (int j = hl * jh; j < min(n, (hl + 1) * jh); ++j) {
-                    const double t = s_Q[wib][j][bl] * s_w[wib][j];
-                    cb -= t;
-                    sc += fabs(t);
+        // projection passes
+        const int jh = (n + 1) / 2, j0 = hl * jh, j1 = min(n, j0 + jh);
+        for (int pass = 0; pass < 6; ++pass) {
+            float2 cb = make_float2(0.0f, 0.0f);
+            float mag = 0.0f;
+            if (bl < l) {
+                FFAcc acc(make_float2(hl == 0 ? (float)c_mono.lap[di][bl] : 0.0f, 0.0f));
+                for (int j = j0; j < j1; ++j) {
+                    acc.sub(Q[j][bl], w[j]);
+                    mag = fmaf(fabsf(Q[j][bl].x), fabsf(w[j].x), mag);
                 }
-            cb += __shfl_xor_sync(0xffffffffu, cb, 16);
-            sc += __shfl_xor_sync(0xffffffffu, sc, 16);
-            if (bl < l) cb += (double)c_mono.lap[di][bl];
-            double cm = (bl < l) ? fabs(cb) / fmax(1.0, sc) : 0.0;
-            for (int o = 16; o; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-            if (cm <= 1e-15) break;
-            const float dc = bl < l ? (float)cb * s_d[wib][bl] : 0.f;
-            float zb = 0.f;
-            for (int a = 0; a < l; ++a) zb = fmaf(G[bl < l ? bl : 0][l + a], __shfl_sync(0xffffffffu, dc, a), zb);
-            if (lane < l) s_z[wib][lane] = zb * s_d[wib][lane];
+                cb = make_float2(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
+                if (hl == 0) mag += fabsf((float)c_mono.lap[di][bl]);
+            }
+            const float oh = __shfl_xor_sync(kFull, cb.x, 16), ol = __shfl_xor_sync(kFull, cb.y, 16);
+            mag += __shfl_xor_sync(kFull, mag, 16);
+            const float2 t = ff_two_sum(cb.x, oh);
+            const float c_b = __fadd_rn(t.x, __fadd_rn(t.y, __fadd_rn(cb.y, ol)));
+            const bool done = __all_sync(kFull, bl >= l || fabsf(c_b) <= 1e-13f * mag);
+            if (done) break;
+            // z = D Ginv D c (lanes 0..l-1)
+            const float dc = bl < l ? c_b * dsc[bl] : 0.0f;
+            float zb = 0.0f;
+            for (int a = 0; a < l; ++a) zb = fmaf(G[bl < l ? bl : 0][a], __shfl_sync(kFull, dc, a), zb);
+            if (lane < l) zz[lane] = zb * dsc[lane];
             __syncwarp();
             if (lane < n) {
-                double corr = 0.0;
-                for (int b = 0; b < l; ++b) corr = fma(s_Q[wib][lane][b], (double)s_z[wib][b], corr);
-                s_w[wib][lane] += corr;
+                FFAcc acc(w[lane]);
+                for (int b = 0; b < l; ++b) acc.sub(Q[lane][b], make_float2(-zz[b], 0.0f));
+                w[lane] = ff_fast_sum(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
             }
             __syncwarp();
         }
         // residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r, e = r - Q lambda
-        if (lane < n) s_w32[wib][lane] = (float)s_w[wib][lane];
-        __syncwarp();
-        float lphi = 0.f;
+        float lphi = 0.0f;
         if (lane < n) {
-            float r2 = 0.f;
-            for (int a = 0; a < DIM; ++a) r2 = fmaf(x32[lane * DIM + a], x32[lane * DIM + a], r2);
+            float r2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) r2 = fmaf(xf[lane * DIM + a].x, xf[lane * DIM + a].x, r2);
             float rk2 = sqrtf(r2);
             for (int i = 3; i < k; i += 2) rk2 *= r2;
             lphi = (float)(k * (k + DIM - 2)) * rk2;
-            float aw = 0.f;
-            for (int j = 0; j < n; ++j) {
-                float d2 = 0.f;
-                for (int a = 0; a < DIM; ++a) {
-                    const float t = x32[lane * DIM + a] - x32[j * DIM + a];
-                    d2 = fmaf(t, t, d2);
-                }
-                float pw = sqrtf(d2);
-                for (int i = 1; i < k; i += 2) pw *= d2;
-                aw = fmaf(pw, s_w32[wib][j], aw);
-            }
-            s_r[wib][lane] = lphi - aw;
+            float aw = 0.0f;
+            for (int j = 0; j < n; ++j) aw = fmaf(A[lane][j], __fadd_rn(w[j].x, w[j].y), aw);
+            rr[lane] = lphi - aw;
         }
         __syncwarp();
-        float qr = 0.f;
-        if (lane < l)
-            for (int j = 0; j < n; ++j) qr = fmaf(s_Q32[wib][j][lane], s_r[wib][j], qr);
-        const float dq = lane < l ? qr * s_d[wib][lane] : 0.f;
-        float lam = 0.f;
-        for (int a = 0; a < l; ++a) lam = fmaf(G[lane < l ? lane : 0][l + a], __shfl_sync(0xffffffffu, dq, a), lam);
-        if (lane < l) s_z[wib][lane] = lam * s_d[wib][lane];
+        float qr = 0.0f;
+        if (bl < l)
+            for (int j = j0; j < j1; ++j) qr = fmaf(Q[j][bl].x, rr[j], qr);
+        qr += __shfl_xor_sync(kFull, qr, 16);
+        const float dq = bl < l ? qr * dsc[bl] : 0.0f;
+        float lam = 0.0f;
+        for (int a = 0; a < l; ++a) lam = fmaf(G[bl < l ? bl : 0][a], __shfl_sync(kFull, dq, a), lam);
         __syncwarp();
-        float e = 0.f;
+        if (lane < l) zz[lane] = lam * dsc[lane];
+        __syncwarp();
+        float e = 0.0f;
         if (lane < n) {
-            float ql = 0.f;
-            for (int b = 0; b < l; ++b) ql = fmaf(s_Q32[wib][lane][b], s_z[wib][b], ql);
-            e = fabsf(s_r[wib][lane] - ql);
+            float ql = 0.0f;
+            for (int b = 0; b < l; ++b) ql = fmaf(Q[lane][b].x, zz[b], ql);
+            e = fabsf(rr[lane] - ql);
         }
         float emax = e, lmax = fabsf(lphi);
         for (int o = 16; o; o >>= 1) {
-            emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-            lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+            emax = fmaxf(emax, __shfl_xor_sync(kFull, emax, o));
+            lmax = fmaxf(lmax, __shfl_xor_sync(kFull, lmax, o));
         }
         const float rho = emax / fmaxf(lmax, 1e-30f);
-        const bool accept = __all_sync(0xffffffffu, ok) && rho <= J.tau && !isnan(rho);
+        const bool accept = __all_sync(kFull, ok) && rho <= J.tau && !isnan(rho);
         if (J.rho_out && lane == 0) J.rho_out[row - P.row_begin] = rho;
         if (accept) {
             const double inv2 = 1.0 / (s * s);
-            if (lane < n) P.vals[0][rb + lane] = s_w[wib][lane] * inv2;
+            if (lane < n) P.vals[0][rb + lane] = ((double)w[lane].x + (double)w[lane].y) * inv2;
             if (P.status && lane == 0) P.status[row] = MM_ST_ACCEPTED;
         } else if (lane == 0) {
             const int slot = atomicAdd(J.fb_count, 1);
