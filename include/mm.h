@@ -74,6 +74,11 @@ extern "C" {
 #define MM_OPT_KAPPA_MAX 3     /* fallback if kappa1 * u32 exceeds (0.1);
                                   kappa1 = ||K||_1 ||K^-1||_1, the second norm
                                   taken exactly from the FP32 inverse         */
+#define MM_OPT_WIDE 4          /* arithmetic of the refinement residuals and of
+                                  the surrogate's consistency projection:      */
+#define MM_WIDE_FF 0           /*   double-FP32 pairs (~48-bit significand,
+                                    compensated sums on the FP32 pipe; default) */
+#define MM_WIDE_FP64 1         /*   native FP64                                */
 
 typedef struct mm_ctx mm_ctx;
 

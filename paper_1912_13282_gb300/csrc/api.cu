@@ -130,7 +130,8 @@ int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream) {
     ctx->num_sms = sms;
     ctx->smem_optin = (size_t)optin;
     if (rbffd_init_device(ctx) != MM_OK || batched_init_device(ctx) != MM_OK ||
-        mlp_init_device(ctx) != MM_OK) {
+        mlp_init_device(ctx) != MM_OK || mixed_init_device_2d(ctx) != MM_OK ||
+        mixed_init_device_3d(ctx) != MM_OK) {
         delete ctx;
         return MM_ECUDA;
     }
@@ -166,6 +167,11 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value) {
         case MM_OPT_KAPPA_MAX:
             if (!(value > 0)) return mm_fail(ctx, MM_EBADARG, "kappa threshold must be > 0");
             ctx->kappa_max = value;
+            return MM_OK;
+        case MM_OPT_WIDE:
+            if (value != MM_WIDE_FF && value != MM_WIDE_FP64)
+                return mm_fail(ctx, MM_EBADARG, "wide arithmetic must be MM_WIDE_FF or MM_WIDE_FP64");
+            ctx->wide64 = value == MM_WIDE_FP64;
             return MM_OK;
     }
     return mm_fail(ctx, MM_EBADARG, "unknown option %d", key);

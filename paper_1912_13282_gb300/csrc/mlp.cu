@@ -435,7 +435,8 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
 //     w = wt + Q z,  (Q^T Q) z = l_q - Q^T w,
 // repeated while the constraint rows are off by more than 1e-13 of their
 // terms (at most 6 passes).  Q, w and the constraint residuals are carried in
-// double-FP32 (compensated sums on the FP32 pipe); z comes from an FP32
+// double-FP32 (compensated sums on the FP32 pipe), or in FP64 when the
+// context asks for native FP64 (MM_OPT_WIDE); z comes from an FP32
 // inverse of the Jacobi-scaled Gram matrix (in-place Gauss-Jordan, no
 // pivoting: the matrix is symmetric positive definite).
 // Residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least
@@ -454,21 +455,23 @@ __device__ __forceinline__ float phs32(float r2, int k) {
     return p;
 }
 
-template <int DIM>
+template <int DIM, bool W64>
 __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjParams J) {
     constexpr int NM = 32, LM = 16, QP = LM + 1, GP = LM + 4;
     const WParams &P = J.P;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    __shared__ double s_xi[4][NM * DIM];          // offsets (FP64, then double-FP32 in place)
-    __shared__ float2 s_Q[4][NM][QP];             // Q (double-FP32)
+    __shared__ double s_xi[4][NM * DIM];          // offsets (FP64; double-FP32 in place unless W64)
+    __shared__ double s_Q[4][NM][QP];             // Q (double-FP32 pairs, or FP64 if W64)
     __shared__ __align__(16) float s_G[4][LM][GP]; // Jacobi-scaled Gram matrix, then its inverse
     __shared__ float s_A[4][NM][NM + 1];          // FP32 phi matrix for the residual check
-    __shared__ float2 s_w[4][NM];                 // weights (double-FP32)
+    __shared__ double s_w[4][NM];                 // weights (double-FP32 pairs, or FP64 if W64)
     __shared__ float s_u[4][LM], s_d[4][LM], s_z[4][LM], s_r[4][NM];
-    float2 (*Q)[QP] = s_Q[wib];
+    float2 (*Qf)[QP] = reinterpret_cast<float2 (*)[QP]>(s_Q[wib]);
+    double (*Qd)[QP] = s_Q[wib];
     float (*G)[GP] = s_G[wib];
     float (*A)[NM + 1] = s_A[wib];
-    float2 *w = s_w[wib];
+    float2 *wf = reinterpret_cast<float2 *>(s_w[wib]);
+    double *wd = s_w[wib];
     float *u = s_u[wib], *dsc = s_d[wib], *zz = s_z[wib], *rr = s_r[wib];
     const int l = P.l, di = DIM - 2, k = P.k;
     const int bl = lane & 15, hl = lane >> 4;
@@ -485,14 +488,27 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             continue;
         }
         float2 *xf = reinterpret_cast<float2 *>(xi);
-        for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
-        __syncwarp();
+        if (!W64) {
+            for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
+            __syncwarp();
+        }
+        // leading FP32 parts of the offsets, Q and w
+        auto x32 = [&](int j, int a) { return W64 ? (float)xi[j * DIM + a] : xf[j * DIM + a].x; };
+        auto q32 = [&](int j, int b) { return W64 ? (float)Qd[j][b] : Qf[j][b].x; };
+        auto w32 = [&](int j) { return W64 ? (float)wd[j] : __fadd_rn(wf[j].x, wf[j].y); };
         // Q by stencil node, predicted weights
         if (lane < n) {
-            float2 *Qj = Q[lane];
-            Qj[0] = make_float2(1.0f, 0.0f);
-            for (int b = 1; b < l; ++b) Qj[b] = ff_mul(Qj[c_mono.parent[di][b]], xf[lane * DIM + c_mono.var[di][b]]);
-            w[lane] = make_float2(J.wt[(row - P.row_begin) * n + lane], 0.0f);
+            if (W64) {
+                double *Qj = Qd[lane];
+                Qj[0] = 1.0;
+                for (int b = 1; b < l; ++b) Qj[b] = Qj[c_mono.parent[di][b]] * xi[lane * DIM + c_mono.var[di][b]];
+                wd[lane] = (double)J.wt[(row - P.row_begin) * n + lane];
+            } else {
+                float2 *Qj = Qf[lane];
+                Qj[0] = make_float2(1.0f, 0.0f);
+                for (int b = 1; b < l; ++b) Qj[b] = ff_mul(Qj[c_mono.parent[di][b]], xf[lane * DIM + c_mono.var[di][b]]);
+                wf[lane] = make_float2(J.wt[(row - P.row_begin) * n + lane], 0.0f);
+            }
         }
         // FP32 phi matrix: unordered pairs (r, (r + d) mod n), each once
         for (int d = 1; d <= n / 2; ++d) {
@@ -503,7 +519,7 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
                 float r2 = 0.0f;
 #pragma unroll
                 for (int a = 0; a < DIM; ++a) {
-                    const float t = xf[r * DIM + a].x - xf[c * DIM + a].x;
+                    const float t = x32(r, a) - x32(c, a);
                     r2 = fmaf(t, t, r2);
                 }
                 const float v = phs32(r2, k);
@@ -519,7 +535,7 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             while (t >= l - a) { t -= l - a; ++a; }
             const int b = a + t;
             float acc = 0.0f;
-            for (int j = 0; j < n; ++j) acc = fmaf(Q[j][a].x, Q[j][b].x, acc);
+            for (int j = 0; j < n; ++j) acc = fmaf(q32(j, a), q32(j, b), acc);
             G[a][b] = acc;
             G[b][a] = acc;
         }
@@ -553,25 +569,42 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             }
             __syncwarp();
         }
-        // projection passes
+        // projection passes; lanes (constraint bl, half hl of the nodes)
         const int jh = (n + 1) / 2, j0 = hl * jh, j1 = min(n, j0 + jh);
         for (int pass = 0; pass < 6; ++pass) {
-            float2 cb = make_float2(0.0f, 0.0f);
-            float mag = 0.0f;
-            if (bl < l) {
-                FFAcc acc(make_float2(hl == 0 ? (float)c_mono.lap[di][bl] : 0.0f, 0.0f));
-                for (int j = j0; j < j1; ++j) {
-                    acc.sub(Q[j][bl], w[j]);
-                    mag = fmaf(fabsf(Q[j][bl].x), fabsf(w[j].x), mag);
+            float c_b = 0.0f, mag = 0.0f;
+            if (W64) {
+                double cb = 0.0;
+                if (bl < l) {
+                    if (hl == 0) cb = (double)c_mono.lap[di][bl];
+                    for (int j = j0; j < j1; ++j) {
+                        cb = fma(-Qd[j][bl], wd[j], cb);
+                        mag = fmaf(fabsf((float)Qd[j][bl]), fabsf((float)wd[j]), mag);
+                    }
                 }
-                cb = make_float2(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
-                if (hl == 0) mag += fabsf((float)c_mono.lap[di][bl]);
+                cb += __shfl_xor_sync(kFull, cb, 16);
+                c_b = (float)cb;
+            } else {
+                float2 cb = make_float2(0.0f, 0.0f);
+                if (bl < l) {
+                    FFAcc acc(make_float2(hl == 0 ? (float)c_mono.lap[di][bl] : 0.0f, 0.0f));
+                    for (int j = j0; j < j1; ++j) {
+                        acc.sub(Qf[j][bl], wf[j]);
+                        mag = fmaf(fabsf(Qf[j][bl].x), fabsf(wf[j].x), mag);
+                    }
+                    cb = make_float2(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
+                }
+                const float oh = __shfl_xor_sync(kFull, cb.x, 16), ol = __shfl_xor_sync(kFull, cb.y, 16);
+                const float2 t = ff_two_sum(cb.x, oh);
+                c_b = __fadd_rn(t.x, __fadd_rn(t.y, __fadd_rn(cb.y, ol)));
             }
-            const float oh = __shfl_xor_sync(kFull, cb.x, 16), ol = __shfl_xor_sync(kFull, cb.y, 16);
             mag += __shfl_xor_sync(kFull, mag, 16);
-            const float2 t = ff_two_sum(cb.x, oh);
-            const float c_b = __fadd_rn(t.x, __fadd_rn(t.y, __fadd_rn(cb.y, ol)));
-            const bool done = __all_sync(kFull, bl >= l || fabsf(c_b) <= 1e-13f * mag);
+            if (bl < l && hl == 0) mag += fabsf((float)c_mono.lap[di][bl]);
+            mag = fmaxf(mag, __shfl_xor_sync(kFull, mag, 16));
+            // stop when every constraint row holds to 1e-13 of its terms
+            // (FP64: 1e-15; both near the rounding level of the sums)
+            const float rtol = W64 ? 1e-15f : 1e-13f;
+            const bool done = __all_sync(kFull, bl >= l || fabsf(c_b) <= rtol * mag);
             if (done) break;
             // z = D Ginv D c (lanes 0..l-1)
             const float dc = bl < l ? c_b * dsc[bl] : 0.0f;
@@ -580,9 +613,15 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             if (lane < l) zz[lane] = zb * dsc[lane];
             __syncwarp();
             if (lane < n) {
-                FFAcc acc(w[lane]);
-                for (int b = 0; b < l; ++b) acc.sub(Q[lane][b], make_float2(-zz[b], 0.0f));
-                w[lane] = ff_fast_sum(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
+                if (W64) {
+                    double corr = 0.0;
+                    for (int b = 0; b < l; ++b) corr = fma(Qd[lane][b], (double)zz[b], corr);
+                    wd[lane] += corr;
+                } else {
+                    FFAcc acc(wf[lane]);
+                    for (int b = 0; b < l; ++b) acc.sub(Qf[lane][b], make_float2(-zz[b], 0.0f));
+                    wf[lane] = ff_fast_sum(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
+                }
             }
             __syncwarp();
         }
@@ -591,18 +630,18 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
         if (lane < n) {
             float r2 = 0.0f;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) r2 = fmaf(xf[lane * DIM + a].x, xf[lane * DIM + a].x, r2);
+            for (int a = 0; a < DIM; ++a) r2 = fmaf(x32(lane, a), x32(lane, a), r2);
             float rk2 = sqrtf(r2);
             for (int i = 3; i < k; i += 2) rk2 *= r2;
             lphi = (float)(k * (k + DIM - 2)) * rk2;
             float aw = 0.0f;
-            for (int j = 0; j < n; ++j) aw = fmaf(A[lane][j], __fadd_rn(w[j].x, w[j].y), aw);
+            for (int j = 0; j < n; ++j) aw = fmaf(A[lane][j], w32(j), aw);
             rr[lane] = lphi - aw;
         }
         __syncwarp();
         float qr = 0.0f;
         if (bl < l)
-            for (int j = j0; j < j1; ++j) qr = fmaf(Q[j][bl].x, rr[j], qr);
+            for (int j = j0; j < j1; ++j) qr = fmaf(q32(j, bl), rr[j], qr);
         qr += __shfl_xor_sync(kFull, qr, 16);
         const float dq = bl < l ? qr * dsc[bl] : 0.0f;
         float lam = 0.0f;
@@ -613,7 +652,7 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
         float e = 0.0f;
         if (lane < n) {
             float ql = 0.0f;
-            for (int b = 0; b < l; ++b) ql = fmaf(Q[lane][b].x, zz[b], ql);
+            for (int b = 0; b < l; ++b) ql = fmaf(q32(lane, b), zz[b], ql);
             e = fabsf(rr[lane] - ql);
         }
         float emax = e, lmax = fabsf(lphi);
@@ -626,7 +665,7 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
         if (J.rho_out && lane == 0) J.rho_out[row - P.row_begin] = rho;
         if (accept) {
             const double inv2 = 1.0 / (s * s);
-            if (lane < n) P.vals[0][rb + lane] = ((double)w[lane].x + (double)w[lane].y) * inv2;
+            if (lane < n) P.vals[0][rb + lane] = (W64 ? wd[lane] : WideFF::to_d(wf[lane])) * inv2;
             if (P.status && lane == 0) P.status[row] = MM_ST_ACCEPTED;
         } else if (lane == 0) {
             const int slot = atomicAdd(J.fb_count, 1);
@@ -1029,7 +1068,8 @@ int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, 
         J.fb_count = cnt;
         J.rho_out = d_rho ? d_rho + (r0 - row_begin) : nullptr;
         const int blocks = (int)std::min<int64_t>((r1 - r0 + 3) / 4, (int64_t)ctx->num_sms * 32);
-        k_project<2><<<blocks, 128, 0, st>>>(J);
+        if (ctx->wide64) k_project<2, true><<<blocks, 128, 0, st>>>(J);
+        else k_project<2, false><<<blocks, 128, 0, st>>>(J);
         MM_LAUNCH_CHECK(ctx);
     }
     // rejected stencils: FP32 + FP64 refinement first if asked, then FP64

@@ -22,6 +22,7 @@ struct mm_ctx {
     double ir_tol = 1e-9;
     int ir_max_steps = 4;
     double kappa_max = 0.1;
+    int wide64 = 0;     // refinement residuals and projection in native FP64
     // tuned launch shapes of the batched weights kernel, by batch signature
     std::map<std::string, mm_launch_config> tiles;
 };
@@ -80,6 +81,11 @@ struct WeightsJob {
 };
 
 int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision);
+// FP32 + refinement kernel of one class (2D / 3D); handed-over rows go to fb_list
+int mixed_launch_2d(mm_ctx *ctx, const WeightsJob &job, int *fb_count, int *fb_list);
+int mixed_launch_3d(mm_ctx *ctx, const WeightsJob &job, int *fb_count, int *fb_list);
+int mixed_init_device_2d(mm_ctx *ctx);
+int mixed_init_device_3d(mm_ctx *ctx);
 int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, int *fb_count,
                            int *fb_list);
 int spmv_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const double *u,

@@ -1,6 +1,7 @@
 // RBF-FD stencil weights on the GPU, one launch per stencil class: one warp
-// per stencil (row), FP64 solver or FP32 + FP64-refinement solver with a queue
-// of stragglers handed to the FP64 solver (see rbffd_dev.cuh for the math).
+// per stencil (row), FP64 solver or FP32 + refinement solver (mixed2d.cu,
+// mixed3d.cu) with a queue of stragglers handed to the FP64 solver (see
+// rbffd_dev.cuh for the math).
 #include "rbffd_dev.cuh"
 
 namespace {
@@ -17,57 +18,6 @@ __global__ void __launch_bounds__(128) k_weights_fp64(WParams P) {
         const int64_t row = P.list ? (int64_t)P.list[t] : P.row_begin + t;
         fp64_row<DIM>(P, row, base, P.list != nullptr);
     }
-}
-
-template <int DIM, int RPL, int R>
-__global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
-    extern __shared__ double smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
-    char *base = (char *)smem + (size_t)wib * Ly.bytes;
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = P.row_begin + gw; row < P.row_end; row += nw) {
-        if (mixed_row<DIM, RPL, R>(P, row, base) && lane == 0) {
-            const int slot = atomicAdd(P.fb_count, 1);
-            P.fb_list[slot] = (int)row;
-        }
-        __syncwarp();
-    }
-}
-
-
-template <int DIM, int RPL, int R>
-int launch_mixed_t(mm_ctx *ctx, const WParams &P, int64_t rows) {
-    const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
-    auto kern = k_weights_mixed<DIM, RPL, R>;
-    int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / Ly.bytes));
-    const size_t sm = Ly.bytes * wpb;
-    if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "stencil too large for shared memory");
-    MM_CUDA_CHECK(ctx, mm_set_smem(ctx, (const void *)kern, sm));
-    const int blocks = (int)std::min<int64_t>((rows + wpb - 1) / wpb, (int64_t)ctx->num_sms * 32);
-    kern<<<blocks, wpb * 32, sm, ctx->stream>>>(P);
-    MM_LAUNCH_CHECK(ctx);
-    return MM_OK;
-}
-
-template <int DIM, int RPL>
-int launch_mixed_r(mm_ctx *ctx, const WParams &P, int64_t rows) {
-    switch (P.R) {
-        case 1: return launch_mixed_t<DIM, RPL, 1>(ctx, P, rows);
-        case 2: return launch_mixed_t<DIM, RPL, 2>(ctx, P, rows);
-        case 3: return launch_mixed_t<DIM, RPL, 3>(ctx, P, rows);
-        case 4: return launch_mixed_t<DIM, RPL, 4>(ctx, P, rows);
-        default: return launch_mixed_t<DIM, RPL, 5>(ctx, P, rows);
-    }
-}
-
-template <int DIM>
-int launch_mixed(mm_ctx *ctx, const WParams &P, int64_t rows) {
-    const int rpl = (P.M_max + 31) / 32;
-    if (rpl <= 1) return launch_mixed_r<DIM, 1>(ctx, P, rows);
-    if (rpl == 2) return launch_mixed_r<DIM, 2>(ctx, P, rows);
-    return launch_mixed_r<DIM, 3>(ctx, P, rows);
 }
 
 }  // namespace
@@ -132,7 +82,8 @@ int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, in
     }
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(P.fb_count, 0, sizeof(int), st));
     {
-        const int rc = dim == 2 ? launch_mixed<2>(ctx, P, rows) : launch_mixed<3>(ctx, P, rows);
+        const int rc = dim == 2 ? mixed_launch_2d(ctx, job, P.fb_count, P.fb_list)
+                                : mixed_launch_3d(ctx, job, P.fb_count, P.fb_list);
         if (rc != MM_OK) return rc;
     }
     return launch_fp64(P.fb_list, P.fb_count, rows);

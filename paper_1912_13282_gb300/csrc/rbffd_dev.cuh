@@ -50,6 +50,7 @@ struct WParams {
     double ir_tol;
     int ir_max_steps;
     double kappa_max;
+    int wide64;                // refinement residuals in native FP64 (else double-FP32)
     // indirect mode (FP64 fallback): rows come from list[0..*count)
     const int *list;
     const int *list_count;
@@ -378,7 +379,7 @@ __device__ __forceinline__ unsigned pivot_key(float v, int r) {
 }
 
 template <int RPL>
-__device__ bool gj32_invert(float *__restrict__ S, int p32, int M, int *step, int *perm,
+__device__ __forceinline__ bool gj32_invert(float *__restrict__ S, int p32, int M, int *step, int *perm,
                             float *__restrict__ ubuf, float tiny) {
     const int lane = threadIdx.x & 31;
     const int C4 = (M + 3) >> 2, W4 = 4 * C4;
@@ -676,7 +677,7 @@ __device__ __forceinline__ float2 ff_phs_km2(float2 r2, int k) {
 // [n x l], B [M x R] (rows < n: l_phi, rows n + b: l_q), from the scaled
 // offsets xf [n x DIM] (double-FP32).  Returns max |K| over A and Q (FP32).
 template <int DIM>
-__device__ float assemble_ff(const WParams &P, int64_t row, int n, const float2 *xf, float2 *A, int pA,
+__device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int n, const float2 *xf, float2 *A, int pA,
                              float2 *Q, float2 *B, int R) {
     const int lane = threadIdx.x & 31;
     const int l = P.l, k = P.k, di = DIM - 2;
@@ -753,6 +754,85 @@ __device__ float assemble_ff(const WParams &P, int64_t row, int n, const float2 
     return warp_maxf(fmaxf(amax, 1.0f));
 }
 
+// The same system in native FP64: A64 [n x pA] (diagonal 0), Q64 [n x l],
+// B64 [M x R] (rows < n: l_phi, rows n + b: l_q).  Returns max |K| (FP32).
+template <int DIM>
+__device__ __noinline__ float assemble_f64(const WParams &P, int64_t row, int n, const double *xi, double *A64, int pA,
+                              double *Q64, double *B64, int R) {
+    const int lane = threadIdx.x & 31;
+    const int l = P.l, k = P.k, di = DIM - 2;
+    double amax = 0.0;
+    for (int d = 1; d <= n / 2; ++d) {
+        const int cnt = (2 * d == n) ? n / 2 : n;
+        for (int r = lane; r < cnt; r += 32) {
+            int c = r + d;
+            if (c >= n) c -= n;
+            double r2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const double t = xi[r * DIM + a] - xi[c * DIM + a];
+                r2 = fma(t, t, r2);
+            }
+            const double v = phs(r2, k);
+            A64[r * pA + c] = v;
+            A64[c * pA + r] = v;
+            amax = fmax(amax, v);
+        }
+    }
+    for (int r = lane; r < n; r += 32) {
+        A64[r * pA + r] = 0.0;
+        double *Qr = Q64 + r * l;
+        Qr[0] = 1.0;
+        for (int b = 1; b < l; ++b) {
+            const double v = Qr[c_mono.parent[di][b]] * xi[r * DIM + c_mono.var[di][b]];
+            Qr[b] = v;
+            amax = fmax(amax, fabs(v));
+        }
+        double r2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) r2 = fma(xi[r * DIM + a], xi[r * DIM + a], r2);
+        double rk2 = sqrt(r2);
+        for (int i = 3; i < k; i += 2) rk2 *= r2;
+        for (int cI = 0; cI < R; ++cI) {
+            const int op = P.opcode[cI];
+            double v;
+            if (cI >= P.R) {
+                v = 0.0;                  // unused solver column
+            } else if (op == 0) {
+                v = (double)(k * (k + DIM - 2)) * rk2;
+            } else {
+                double dot;
+                if (op == 4) {
+                    dot = 0.0;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) dot = fma(P.normals[row * DIM + a], xi[r * DIM + a], dot);
+                } else {
+                    dot = xi[r * DIM + (op - 1)];
+                }
+                v = -(double)k * rk2 * dot;
+            }
+            B64[r * R + cI] = v;
+        }
+    }
+    for (int b = lane; b < l; b += 32) {
+        for (int cI = 0; cI < R; ++cI) {
+            const int op = P.opcode[cI];
+            double v = 0.0;
+            if (cI < P.R) {
+                if (op == 0) {
+                    v = (double)c_mono.lap[di][b];
+                } else {
+                    const int a = c_mono.lin[di][b];
+                    if (a >= 0) v = op == 4 ? P.normals[row * DIM + a] : ((a == op - 1) ? 1.0 : 0.0);
+                }
+            }
+            B64[(n + b) * R + cI] = v;
+        }
+    }
+    __syncwarp();
+    return warp_maxf(fmaxf((float)amax, 1.0f));
+}
+
 // Compensated dot product (Ogita, Rump & Oishi) in double-FP32: acc -= kx * xx.
 // The product of the high parts is split exactly and subtracted from hi with
 // TwoSum; the rounding errors go to lo and the cross terms to la and lb (three
@@ -773,6 +853,121 @@ struct FFAcc {
     __device__ __forceinline__ float value() const { return __fadd_rn(hi, __fadd_rn(lo, __fadd_rn(la, lb))); }
 };
 
+// The wide arithmetic of the refinement: the system (A, Q, b) and the
+// solution x as double-FP32 pairs (WideFF, on the FP32 pipe) or as FP64
+// (Wide64); the residual of row i, column c over the nonzero blocks of K.
+struct WideFF {
+    using T = float2;
+    static __device__ __forceinline__ float hi(T v) { return v.x; }
+    static __device__ __forceinline__ T from_f(float d) { return make_float2(d, 0.0f); }
+    static __device__ __forceinline__ T add_f(T x, float d) {
+        const float2 t = ff_two_sum(x.x, d);
+        return ff_fast_sum(t.x, __fadd_rn(t.y, x.y));
+    }
+    static __device__ __forceinline__ double to_d(T x) { return (double)x.x + (double)x.y; }
+    static __device__ __forceinline__ float residual(const T *A, int pA, const T *Q, int l, const T *B,
+                                                     const T *X, int n, int R, int i, int c) {
+        FFAcc acc(B[i * R + c]);
+        if (i < n) {
+            const T *Ai = A + i * pA;
+            const T *Qi = Q + i * l;
+            for (int j = 0; j < n; ++j) acc.sub(Ai[j], X[j * R + c]);
+            for (int b = 0; b < l; ++b) acc.sub(Qi[b], X[(n + b) * R + c]);
+        } else {
+            const int b = i - n;
+            for (int j = 0; j < n; ++j) acc.sub(Q[j * l + b], X[j * R + c]);
+        }
+        return acc.value();
+    }
+};
+
+struct Wide64 {
+    using T = double;
+    static __device__ __forceinline__ float hi(T v) { return (float)v; }
+    static __device__ __forceinline__ T from_f(float d) { return (double)d; }
+    static __device__ __forceinline__ T add_f(T x, float d) { return x + (double)d; }
+    static __device__ __forceinline__ double to_d(T x) { return x; }
+    static __device__ __forceinline__ float residual(const T *A, int pA, const T *Q, int l, const T *B,
+                                                     const T *X, int n, int R, int i, int c) {
+        double acc = B[i * R + c];
+        if (i < n) {
+            const T *Ai = A + i * pA;
+            const T *Qi = Q + i * l;
+            for (int j = 0; j < n; ++j) acc = fma(-Ai[j], X[j * R + c], acc);
+            for (int b = 0; b < l; ++b) acc = fma(-Qi[b], X[(n + b) * R + c], acc);
+        } else {
+            const int b = i - n;
+            for (int j = 0; j < n; ++j) acc = fma(-Q[j * l + b], X[j * R + c], acc);
+        }
+        return (float)acc;
+    }
+};
+
+// Refinement after the FP32 inverse: x0 = K^-1 b, then x <- x + K^-1 (b - K x)
+// for at least two steps and until the observed contraction shows the
+// remaining error below the tolerance; then one correction from the
+// constraint rows alone.  Returns false if it did not converge.
+template <int RPL, int R, class Wd>
+__device__ __forceinline__ bool mixed_refine(const WParams &P, int n, int M, const float *S, int p32, const int *step,
+                             const int *perm, const typename Wd::T *Aw, int pA, const typename Wd::T *Qw,
+                             const typename Wd::T *Bw, typename Wd::T *Xw, float *V32, float *Bp) {
+    const int lane = threadIdx.x & 31, l = P.l;
+    for (int e = lane; e < M * R; e += 32) V32[e] = Wd::hi(Bw[e]);
+    __syncwarp();
+    gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
+    float dmax = 0.0f;
+    for (int e = lane; e < M * R; e += 32) {
+        const float d = V32[e];
+        Xw[e] = Wd::from_f(d);
+        dmax = fmaxf(dmax, fabsf(d));
+    }
+    float dprev = warp_maxf(dmax);
+    __syncwarp();
+    bool conv = false;
+    for (int it = 1; it <= P.ir_max_steps; ++it) {
+        for (int e = lane; e < M * R; e += 32) {
+            const int i = e / R, c = e - i * R;
+            V32[e] = Wd::residual(Aw, pA, Qw, l, Bw, Xw, n, R, i, c);
+        }
+        __syncwarp();
+        gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
+        float dmx = 0.0f, xmax = 0.0f;
+        for (int e = lane; e < M * R; e += 32) {
+            const float d = V32[e];
+            const typename Wd::T xn = Wd::add_f(Xw[e], d);
+            Xw[e] = xn;
+            dmx = fmaxf(dmx, fabsf(d));
+            if (e < n * R) xmax = fmaxf(xmax, fabsf(Wd::hi(xn)));
+        }
+        dmx = warp_maxf(dmx);
+        xmax = warp_maxf(xmax);
+        // the observed contraction of the last step bounds the error left;
+        // it is taken from two corrections (the first step's ratio compares
+        // a correction with the solution itself and can underestimate it)
+        const float theta = dmx / fmaxf(dprev, 1e-30f);
+        if (it >= 2 && theta < 0.5f && theta / (1.0f - theta) * dmx <= (float)P.ir_tol * xmax) {
+            conv = true;
+            break;
+        }
+        dprev = dmx;
+        __syncwarp();
+    }
+    if (!conv) return false;
+    // Constraint rows Q^T w = l_q: one more residual on those rows only,
+    // corrected through the FP32 inverse, so the monomials are reproduced to
+    // the residual's precision rather than to the refinement tolerance.
+    __syncwarp();
+    for (int e = lane; e < M * R; e += 32) {
+        const int i = e / R, c = e - i * R;
+        V32[e] = i >= n ? Wd::residual(Aw, pA, Qw, l, Bw, Xw, n, R, i, c) : 0.0f;
+    }
+    __syncwarp();
+    gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
+    for (int e = lane; e < n * R; e += 32) Xw[e] = Wd::add_f(Xw[e], V32[e]);
+    __syncwarp();
+    return true;
+}
+
 // One stencil (row) with the FP32 + refinement solver; `base` is the warp's
 // shared memory.  Returns true if the row must go to the FP64 solver (its
 // status is then MM_ST_NONCONVERGED and its weights are not written).
@@ -781,20 +976,12 @@ struct FFAcc {
 // product with that inverse.  The 1-norm condition number of K follows from
 // ||K||_1 and the exact infinity norm of the computed inverse (K is
 // symmetric, so both norms agree); a stencil with ||K|| ||K^-1|| u32 above
-// the bound goes to the FP64 solver.  Refinement: x <- x + K^-1 (b - K x),
-// with K, b and x held in double-FP32 and the residual accumulated by a
-// compensated dot product, for at least two steps and until the observed
-// contraction shows the remaining error below the tolerance.  A last
-// correction from the constraint rows alone makes the monomials hold to the
-// residual's precision rather than to the refinement tolerance.
+// the bound goes to the FP64 solver.  The refinement (mixed_refine) keeps K,
+// b and x in double-FP32 with compensated residuals, or in FP64 (P.wide64).
 template <int DIM, int RPL, int R>
 __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base) {
     const int lane = threadIdx.x & 31;
     const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
-    float2 *Af = (float2 *)(base + Ly.a64);
-    float2 *Qf = (float2 *)(base + Ly.q64);
-    float2 *Bf = (float2 *)(base + Ly.b64);
-    float2 *Xf = (float2 *)(base + Ly.x64);
     double *xi = (double *)(base + Ly.xi);
     float *S = (float *)(base + Ly.a32);
     float *U32 = (float *)(base + Ly.u32);
@@ -812,24 +999,43 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
         return false;
     }
     const int M = n + l, W4 = 4 * ((M + 3) >> 2);
-    // scaled offsets to double-FP32, in place (same 8 bytes per coordinate)
-    float2 *xf = reinterpret_cast<float2 *>(xi);
-    for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
-    __syncwarp();
-    const float amax = assemble_ff<DIM>(P, row, n, xf, Af, pA, Qf, Bf, R);
-    // FP32 system: the high parts (own rows; Q^T entries written by the row's owner)
+    // the system in wide arithmetic (A [n x pA], Q [n x l], b [M x R]; 8 bytes per entry)
+    float amax;
+    if (P.wide64) {
+        amax = assemble_f64<DIM>(P, row, n, xi, (double *)(base + Ly.a64), pA, (double *)(base + Ly.q64),
+                                 (double *)(base + Ly.b64), R);
+    } else {
+        // scaled offsets to double-FP32, in place (same 8 bytes per coordinate)
+        float2 *xf = reinterpret_cast<float2 *>(xi);
+        for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
+        __syncwarp();
+        amax = assemble_ff<DIM>(P, row, n, xf, (float2 *)(base + Ly.a64), pA, (float2 *)(base + Ly.q64),
+                                (float2 *)(base + Ly.b64), R);
+    }
+    // FP32 system: the leading parts (own rows; Q^T entries written by the row's owner)
     int step[RPL];
+    const double *A64 = (const double *)(base + Ly.a64), *Q64 = (const double *)(base + Ly.q64);
+    const float2 *Af = (const float2 *)(base + Ly.a64), *Qf = (const float2 *)(base + Ly.q64);
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
         const int r = lane + 32 * q;
         step[q] = r < M ? kBig : -1;
         if (r < n) {
             float *Sr = S + r * p32;
-            for (int c = 0; c < n; ++c) Sr[c] = Af[r * pA + c].x;
-            for (int b = 0; b < l; ++b) {
-                const float v = Qf[r * l + b].x;
-                Sr[n + b] = v;
-                S[(n + b) * p32 + r] = v;
+            if (P.wide64) {
+                for (int c = 0; c < n; ++c) Sr[c] = (float)A64[r * pA + c];
+                for (int b = 0; b < l; ++b) {
+                    const float v = (float)Q64[r * l + b];
+                    Sr[n + b] = v;
+                    S[(n + b) * p32 + r] = v;
+                }
+            } else {
+                for (int c = 0; c < n; ++c) Sr[c] = Af[r * pA + c].x;
+                for (int b = 0; b < l; ++b) {
+                    const float v = Qf[r * l + b].x;
+                    Sr[n + b] = v;
+                    S[(n + b) * p32 + r] = v;
+                }
             }
         } else if (r < M) {
             for (int c = n; c < M; ++c) S[r * p32 + c] = 0.0f;
@@ -866,80 +1072,14 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
     }
     bool conv = false;
     if (!queue) {
-        for (int e = lane; e < M * R; e += 32) V32[e] = Bf[e].x;
-        __syncwarp();
-        gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
-        float dmax = 0.0f;
-        for (int e = lane; e < M * R; e += 32) {
-            const float d = V32[e];
-            Xf[e] = make_float2(d, 0.0f);
-            dmax = fmaxf(dmax, fabsf(d));
-        }
-        float dprev = warp_maxf(dmax);
-        __syncwarp();
-        for (int it = 1; it <= P.ir_max_steps; ++it) {
-            // residual b - K x over the nonzero blocks
-            for (int e = lane; e < M * R; e += 32) {
-                const int i = e / R, c = e - i * R;
-                FFAcc acc(Bf[e]);
-                if (i < n) {
-                    const float2 *Ai = Af + i * pA;
-                    const float2 *Qi = Qf + i * l;
-                    for (int j = 0; j < n; ++j) acc.sub(Ai[j], Xf[j * R + c]);
-                    for (int b = 0; b < l; ++b) acc.sub(Qi[b], Xf[(n + b) * R + c]);
-                } else {
-                    const int b = i - n;
-                    for (int j = 0; j < n; ++j) acc.sub(Qf[j * l + b], Xf[j * R + c]);
-                }
-                V32[e] = acc.value();
-            }
-            __syncwarp();
-            gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
-            float dmx = 0.0f, xmax = 0.0f;
-            for (int e = lane; e < M * R; e += 32) {
-                const float d = V32[e];
-                const float2 x = Xf[e];
-                const float2 t = ff_two_sum(x.x, d);
-                const float2 xn = ff_fast_sum(t.x, __fadd_rn(t.y, x.y));
-                Xf[e] = xn;
-                dmx = fmaxf(dmx, fabsf(d));
-                if (e < n * R) xmax = fmaxf(xmax, fabsf(xn.x));
-            }
-            dmx = warp_maxf(dmx);
-            xmax = warp_maxf(xmax);
-            // the observed contraction of the last step bounds the error left;
-            // it is taken from two corrections (the first step's ratio compares
-            // a correction with the solution itself and can underestimate it)
-            const float theta = dmx / fmaxf(dprev, 1e-30f);
-            if (it >= 2 && theta < 0.5f && theta / (1.0f - theta) * dmx <= (float)P.ir_tol * xmax) {
-                conv = true;
-                break;
-            }
-            dprev = dmx;
-            __syncwarp();
-        }
-        if (conv) {
-            __syncwarp();
-            for (int e = lane; e < M * R; e += 32) {
-                const int i = e / R, c = e - i * R;
-                float r = 0.0f;
-                if (i >= n) {
-                    const int b = i - n;
-                    FFAcc acc(Bf[e]);
-                    for (int j = 0; j < n; ++j) acc.sub(Qf[j * l + b], Xf[j * R + c]);
-                    r = acc.value();
-                }
-                V32[e] = r;
-            }
-            __syncwarp();
-            gj32_apply<RPL, R>(S, p32, M, step, perm, V32, Bp);
-            for (int e = lane; e < n * R; e += 32) {
-                const float2 x = Xf[e];
-                const float2 t = ff_two_sum(x.x, V32[e]);
-                Xf[e] = ff_fast_sum(t.x, __fadd_rn(t.y, x.y));
-            }
-            __syncwarp();
-        }
+        if (P.wide64)
+            conv = mixed_refine<RPL, R, Wide64>(P, n, M, S, p32, step, perm, A64, pA, Q64,
+                                                (const double *)(base + Ly.b64), (double *)(base + Ly.x64),
+                                                V32, Bp);
+        else
+            conv = mixed_refine<RPL, R, WideFF>(P, n, M, S, p32, step, perm, Af, pA, Qf,
+                                                (const float2 *)(base + Ly.b64), (float2 *)(base + Ly.x64),
+                                                V32, Bp);
     }
     if (!conv) {
         if (P.status && lane == 0) P.status[row] = MM_ST_NONCONVERGED;
@@ -951,9 +1091,12 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
     for (int cI = 0; cI < P.R; ++cI) {
         const double sc = P.opcode[cI] == 0 ? inv_s * inv_s : inv_s;
         double *out = P.vals[cI] + rb;
-        for (int j = lane; j < n; j += 32) {
-            const float2 x = Xf[j * R + cI];
-            out[j] = ((double)x.x + (double)x.y) * sc;
+        if (P.wide64) {
+            const double *X = (const double *)(base + Ly.x64);
+            for (int j = lane; j < n; j += 32) out[j] = X[j * R + cI] * sc;
+        } else {
+            const float2 *X = (const float2 *)(base + Ly.x64);
+            for (int j = lane; j < n; j += 32) out[j] = WideFF::to_d(X[j * R + cI]) * sc;
         }
     }
     if (P.status && lane == 0) P.status[row] = MM_ST_OK;
@@ -991,6 +1134,7 @@ inline WParams wparams_from_job(const mm_ctx *ctx, const WeightsJob &job) {
     P.ir_tol = ctx->ir_tol;
     P.ir_max_steps = ctx->ir_max_steps;
     P.kappa_max = ctx->kappa_max;
+    P.wide64 = ctx->wide64;
     return P;
 }
 

@@ -31,3 +31,19 @@ def test_library_exports_every_declared_symbol():
 def test_binding_covers_the_header():
     from paper_1912_13282_gb300 import binding
     assert sorted(binding.EXPORTS) == sorted(declared_functions())
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/mm.h that the binding mirrors (same
+    name, with or without the MM_ prefix) has the same value there."""
+    from paper_1912_13282_gb300 import binding
+    text = open(os.path.join(ROOT, "include", "mm.h")).read()
+    defines = dict((k, int(v)) for k, v in re.findall(r"^#define\s+(MM_\w+)\s+\(?(-?\d+)\)?", text, flags=re.M))
+    checked = 0
+    for name, value in defines.items():
+        for alias in (name, name[3:]):
+            if hasattr(binding, alias):
+                assert getattr(binding, alias) == value, (name, alias)
+                checked += 1
+                break
+    assert checked >= 20 and "MM_OPT_WIDE" in defines and binding.OPT_WIDE == defines["MM_OPT_WIDE"]

@@ -122,12 +122,22 @@ def test_training_reduces_loss(trained):
     assert last < 0.8 * first, (first, last)
 
 
-def test_surrogate_weights_path(P, ctx, oracle, trained):
+@pytest.mark.parametrize("wide", ["ff", "fp64"])
+def test_surrogate_weights_path(P, ctx, oracle, trained, wide):
     """Held-out stencils: accepted rows reproduce the monomials to 1e-12 and
     equal the oracle's FP64 projection of the same prediction; rejected rows
-    equal the FP64 solve; the residual check's rho agrees with the oracle's."""
+    equal the FP64 solve; the residual check's rho agrees with the oracle's.
+    The projection runs in double-FP32 (ff) or native FP64."""
     from paper_1912_13282_gb300 import surrogate as S
     net, _ = trained
+    ctx.set_option(P.binding.OPT_WIDE, P.binding.WIDE_FP64 if wide == "fp64" else P.binding.WIDE_FF)
+    try:
+        _surrogate_path_checks(P, ctx, oracle, net, S)
+    finally:
+        ctx.set_option(P.binding.OPT_WIDE, P.binding.WIDE_FF)
+
+
+def _surrogate_path_checks(P, ctx, oracle, net, S):
     count = 4096
     pts, rp, col = S.make_stencils(ctx, count, seed=10 ** 6)
     n, k, m = 25, 5, 4

@@ -194,11 +194,17 @@ def weight_inputs(P, ctx):
 
 
 @pytest.mark.parametrize("name", ["square", "disk", "ball"])
-@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir", "fp32_ir_wide64"])
 def test_weights_match_oracle(P, ctx, oracle, weight_inputs, name, precision):
+    """fp32_ir refines with double-FP32 residuals (the default), fp32_ir_wide64
+    with native FP64 residuals; both meet the same bar."""
     ns, rp, col, cls = weight_inputs(name)
     prec = P.FP64 if precision == "fp64" else P.FP32_IR
-    got, status = run_gpu_weights(ctx, P, ns, rp, col, cls, prec)
+    ctx.set_option(P.binding.OPT_WIDE, P.binding.WIDE_FP64 if precision.endswith("wide64") else P.binding.WIDE_FF)
+    try:
+        got, status = run_gpu_weights(ctx, P, ns, rp, col, cls, prec)
+    finally:
+        ctx.set_option(P.binding.OPT_WIDE, P.binding.WIDE_FF)
     ok_codes = {0} if precision == "fp64" else {0, P.binding.ST_FALLBACK}
     assert set(np.unique(status)) <= ok_codes, np.unique(status, return_counts=True)
     rng = np.random.default_rng(0)
