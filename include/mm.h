@@ -79,6 +79,9 @@ extern "C" {
 #define MM_WIDE_FF 0           /*   double-FP32 pairs (~48-bit significand,
                                     compensated sums on the FP32 pipe; default) */
 #define MM_WIDE_FP64 1         /*   native FP64                                */
+#define MM_OPT_MLP_INFER 5     /* MLP inference (mm_mlp_forward, surrogate):    */
+#define MM_MLP_FUSED 0         /*   one fused tensor-core kernel (default)     */
+#define MM_MLP_LAYERED 1       /*   layer-by-layer GEMMs (the training path)   */
 
 typedef struct mm_ctx mm_ctx;
 
@@ -313,7 +316,11 @@ int mm_mlp_set_params(mm_ctx *ctx, mm_mlp *net, const float *h_params);
 int mm_mlp_get_params(mm_ctx *ctx, const mm_mlp *net, float *h_params);
 /* Output scaling: targets are learned as (y - mean[c]) / std[c]; host arrays [n_out]. */
 int mm_mlp_set_output_scaling(mm_ctx *ctx, mm_mlp *net, const float *h_mean, const float *h_std);
-/* d_y [B x n_out] = network(d_x [B x n_in]) (FP32 in and out, scaling undone). */
+/* d_y [B x n_out] = network(d_x [B x n_in]) (FP32 in and out, scaling undone).
+ * By default one fused tensor-core kernel (tcgen05, activations kept on chip);
+ * MM_OPT_MLP_INFER = MM_MLP_LAYERED runs the layer-by-layer training path.  A
+ * fused launch whose internal waits time out writes NaN for the affected rows
+ * (never observed; it guards against a hang). */
 int mm_mlp_forward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, float *d_y);
 /* One Adam step (lr; beta 0.9/0.999, eps 1e-8) on the mean squared error over
  * B <= 65536 rows of targets d_t [B x n_out]; d_loss (device, optional)

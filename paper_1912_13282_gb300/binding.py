@@ -20,8 +20,9 @@ ST_OK, ST_SINGULAR, ST_NONCONVERGED, ST_FALLBACK, ST_BADARG, ST_DUPLICATE, ST_AC
 LAP, DX, DY, DZ, DN = 1, 2, 4, 8, 16
 FP64, FP32_IR = 0, 1
 KNN_AUTO, KNN_BRUTE, KNN_GRID = 0, 1, 2
-OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX, OPT_WIDE = 1, 2, 3, 4
+OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX, OPT_WIDE, OPT_MLP_INFER = 1, 2, 3, 4, 5
 WIDE_FF, WIDE_FP64 = 0, 1
+MLP_FUSED, MLP_LAYERED = 0, 1
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",

@@ -173,6 +173,11 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value) {
                 return mm_fail(ctx, MM_EBADARG, "wide arithmetic must be MM_WIDE_FF or MM_WIDE_FP64");
             ctx->wide64 = value == MM_WIDE_FP64;
             return MM_OK;
+        case MM_OPT_MLP_INFER:
+            if (value != MM_MLP_FUSED && value != MM_MLP_LAYERED)
+                return mm_fail(ctx, MM_EBADARG, "MLP inference must be MM_MLP_FUSED or MM_MLP_LAYERED");
+            ctx->mlp_layered = value == MM_MLP_LAYERED;
+            return MM_OK;
     }
     return mm_fail(ctx, MM_EBADARG, "unknown option %d", key);
 }

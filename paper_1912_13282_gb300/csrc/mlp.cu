@@ -37,6 +37,8 @@ struct mm_mlp {
     float *loss = nullptr;              // [1]
     float *part = nullptr;              // [64][256][256] split-K / bias partial sums
     float *ymean = nullptr, *ystd = nullptr;   // [32] output scaling (device)
+    __nv_bfloat16 *img = nullptr;       // weight image of the fused tensor-core inference
+    int *tc_err = nullptr;              // its timeout flag
     std::vector<float> h_mean, h_std;
     int64_t np_pad = 0;
     // offsets into the padded parameter vector
@@ -64,13 +66,20 @@ struct EpiParams {
     bf16 *h;   int ldh;                // bf16 output (activation or dZ)
 };
 
+// GELU (tanh form) with the hardware tanh approximation, as in the fused
+// inference kernel
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float gelu_f(float z) {
     const float c = 0.7978845608028654f;
-    return 0.5f * z * (1.0f + tanhf(c * (z + 0.044715f * z * z * z)));
+    return 0.5f * z * (1.0f + tanh_hw(c * fmaf(0.044715f * z, z * z, z)));
 }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     const float c = 0.7978845608028654f;
-    const float t = tanhf(c * (z + 0.044715f * z * z * z));
+    const float t = tanh_hw(c * fmaf(0.044715f * z, z * z, z));
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * z * z);
 }
 
@@ -378,6 +387,8 @@ int refresh_bf16(mm_ctx *ctx, mm_mlp *net) {
     k_refresh_bf16<<<grid1(ctx, n1 + 2 * n2 + n4), 256, 0, ctx->stream>>>(
         net->p, net->wb, net->oW[0], n1, net->oW[1], n2, net->oW[2], n2, net->oW[3], n4);
     MM_LAUNCH_CHECK(ctx);
+    const int rc = mlp_tc_image(ctx, net->p, net->oW, net->img);
+    if (rc != MM_OK) return rc;
     return MM_OK;
 }
 
@@ -396,21 +407,24 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t row = r0 + gw; row < r1; row += nw) {
         const int64_t b = rp[row];
+        // offsets: the difference in FP64 (it may cancel), the rest in FP32
+        // (the features feed a BF16 network)
         double d[DIM] = {};
-        double r2 = 0.0;
+        float f[DIM] = {};
+        float r2 = 0.0f;
         if (lane < n) {
             const int j = col[b + lane];
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
                 d[a] = pts[(int64_t)j * DIM + a] - pts[row * DIM + a];
-                r2 = fma(d[a], d[a], r2);
+                f[a] = (float)d[a];
+                r2 = fmaf(f[a], f[a], r2);
             }
         }
-        for (int o = 16; o; o >>= 1) r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
-        const double s = sqrt(r2);
-        float f[DIM];
+        for (int o = 16; o; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+        const float inv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) f[a] = (float)(d[a] / s);
+        for (int a = 0; a < DIM; ++a) f[a] *= inv;
         if (DIM == 2 && orient && n >= 3) {
             const float ax = __shfl_sync(0xffffffffu, f[0], 1), ay = __shfl_sync(0xffffffffu, f[1], 1);
             const float an = sqrtf(ax * ax + ay * ay);
@@ -424,7 +438,14 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
 #pragma unroll
             for (int a = 0; a < DIM; ++a) x[(row - r0) * (int64_t)n * DIM + lane * DIM + a] = f[a];
         }
-        if (lane == 0 && scale) scale[row - r0] = s;
+        if (scale) {
+            // s = max distance in FP64, as the weights solvers scale
+            double q2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) q2 = fma(d[a], d[a], q2);
+            for (int o = 16; o; o >>= 1) q2 = fmax(q2, __shfl_xor_sync(0xffffffffu, q2, o));
+            if (lane == 0) scale[row - r0] = sqrt(q2);
+        }
     }
 }
 
@@ -776,7 +797,7 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     const size_t npart = (size_t)64 * kH * kH;
     size_t bytes_f = sizeof(float) * (size_t)(4 * off + 3 * B * kH + B * kKOUT + 1 + 2 * kKOUT + npart);
     size_t bytes_h = sizeof(bf16) * (size_t)(wsz[0] + wsz[1] + wsz[2] + wsz[3] + 3 * B * kH + B * kKIN +
-                                             B * kKOUT + 2 * B * kH);
+                                             B * kKOUT + 2 * B * kH + kMlpTcImageElems) + 256;
     char *fb = nullptr, *hb = nullptr;
     if (cudaMalloc(&fb, bytes_f) != cudaSuccess || cudaMalloc(&hb, bytes_h) != cudaSuccess) {
         cudaGetLastError();
@@ -801,7 +822,9 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     net->Xb = h; h += B * kKIN;
     net->dY = h; h += B * kKOUT;
     net->dZa = h; h += B * kH;
-    net->dZb = h;
+    net->dZb = h; h += B * kH;
+    net->img = h; h += kMlpTcImageElems;     // offsets so far are multiples of 256 elements
+    net->tc_err = (int *)h;
     // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases (plain layout)
     std::mt19937_64 rng(seed);
     std::vector<float> plain((size_t)plain_count(n_in, n_out));
@@ -821,6 +844,7 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     cudaError_t e = cudaMemcpy(net->p, pad.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(net->am, 0, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMemset(net->av, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(net->tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(net->ymean, net->h_mean.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(net->ystd, net->h_std.data(), sizeof(float) * kKOUT, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -894,6 +918,24 @@ int mm_mlp_forward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, float 
     if (!ctx || !net || B < 0 || (B > 0 && (!d_x || !d_y))) return MM_EBADARG;
     ctx->err.clear();
     DeviceGuard g(ctx);
+    if (!ctx->mlp_layered) {
+        // fused inference on the tensor cores, all rows in one launch
+        MlpTcArgs a{};
+        a.x = d_x;
+        a.n_in = net->n_in;
+        a.B = B;
+        a.img = net->img;
+        a.b1 = net->p + net->ob[0];
+        a.b2 = net->p + net->ob[1];
+        a.b3 = net->p + net->ob[2];
+        a.b4 = net->p + net->ob[3];
+        a.ymean = net->ymean;
+        a.ystd = net->ystd;
+        a.n_out = net->n_out;
+        a.y = d_y;
+        a.err = net->tc_err;
+        return mlp_tc_forward(ctx, a);
+    }
     for (int64_t b0 = 0; b0 < B; b0 += net->bmax) {
         const int64_t bs = std::min(net->bmax, B - b0);
         k_pack_x<<<grid1(ctx, bs * kKIN), 256, 0, ctx->stream>>>(d_x + b0 * net->n_in, bs, net->n_in, net->Xb);

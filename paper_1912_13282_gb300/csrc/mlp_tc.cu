@@ -1,0 +1,357 @@
+// Fused inference of the surrogate MLP on the Blackwell tensor cores:
+// Y = W4 gelu(W3 gelu(W2 gelu(W1 X + b1) + b2) + b3) + b4, denormalised.
+//
+// One CTA per SM walks tiles of 128 rows.  The activations of a tile stay in
+// shared memory between layers (two 64 KB buffers, 128B-swizzled K-major
+// layout); each layer is a chain of tcgen05.mma (M = 128, K = 16, BF16 in,
+// FP32 accumulators in tensor memory) issued by one thread; weights stream
+// from a pre-swizzled image in global memory through a two-slot ring of bulk
+// copies (cp.async.bulk + mbarrier transaction counts), except the output
+// layer's, which stay resident.  Eight epilogue warps read the accumulators
+// (tcgen05.ld), add the bias, apply GELU, round to BF16 and write the next
+// layer's input.  Roles:
+//   warp 0      weight producer (one lane)
+//   warp 1      tensor-memory allocation and MMA issue (one lane)
+//   warps 2..9  feature load, epilogues, output store
+// Every mbarrier wait is bounded: on a timeout the kernel records an error
+// and writes NaN for the rows it did not finish, so callers that check their
+// outputs (the surrogate's residual check) reject those rows.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "mm_internal.cuh"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+constexpr int kTileM = 128, kH = 256, kKIN = 64, kKOUT = 32;
+constexpr int kThreads = 320;
+// shared memory map (bytes from a 1024-aligned base)
+constexpr uint32_t kA0 = 0, kA1 = 65536, kRing = 131072, kSlot = 32768, kW4 = 196608,
+                   kBar = 212992, kTmemSlot = kBar + 128, kSmemUsed = kBar + 256;   // 10 barriers below kTmemSlot
+constexpr uint32_t kSmemBytes = kSmemUsed + 1024;   // slack for aligning the base
+// weight image (bf16 elements): W1 one 32 KB block, W2 and W3 four each, W4 four of 4 KB
+constexpr int64_t kImgW1 = 0, kImgW2 = 16384, kImgW3 = 16384 * 5, kImgW4 = 16384 * 9;
+constexpr uint32_t kSpin = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (row, k) inside a K-major 128B-swizzled operand whose
+// K-blocks of 64 elements are `block_bytes` apart (8-row groups 1024 bytes apart)
+__host__ __device__ __forceinline__ uint32_t sw128_offset(int row, int k, uint32_t block_bytes) {
+    return (uint32_t)(k >> 6) * block_bytes + (uint32_t)row * 128u +
+           ((uint32_t)(((k & 63) >> 3) ^ (row & 7)) << 4) + (uint32_t)(k & 7) * 2u;
+}
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+// waits for the phase of the given parity to complete; false after kSpin polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpin; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- tcgen05
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
+}
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu_tc(float z) {
+    const float c = 0.7978845608028654f;
+    return 0.5f * z * (1.0f + tanh_approx(c * fmaf(0.044715f * z, z * z, z)));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ MlpTcArgs A) {
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte aligned base (the 128B swizzle pattern repeats every 1024 bytes)
+    uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t sbase = smem_u32(sm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // barriers: 0,1 ring full; 2,3 ring empty; 4 W4 full; 5 x ready; 6 act ready; 7 acc hidden;
+    // 8 acc out; 9 final drain of the MMA thread's work
+    auto bar = [&](int i) { return sbase + kBar + 8u * (uint32_t)i; };
+    const int64_t ntiles = (A.B + kTileM - 1) / kTileM;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(bar(i), 1);
+        mbar_init(bar(5), 8);
+        mbar_init(bar(6), 8);
+        mbar_init(bar(7), 1);
+        mbar_init(bar(8), 1);
+        mbar_init(bar(9), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(sbase + kTmemSlot)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(sm + kTmemSlot);
+    bool ok = true;
+
+    if (warp == 0) {
+        // ------------------------------------------------ weight producer
+        if (lane == 0) {
+            mbar_expect_tx(bar(4), 16384);
+            bulk_g2s(sbase + kW4, A.img + kImgW4, 16384, bar(4));
+            uint32_t slot = 0, phase = 0;
+            int64_t issued[2] = {0, 0};
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int blk = 0; blk < 9 && ok; ++blk) {
+                    ok = mbar_wait(bar(2 + slot), phase ^ 1u);
+                    if (!ok) break;
+                    mbar_expect_tx(bar(slot), kSlot);
+                    bulk_g2s(sbase + kRing + slot * kSlot, A.img + (int64_t)blk * 16384, kSlot, bar(slot));
+                    ++issued[slot];
+                    if (++slot == 2) { slot = 0; phase ^= 1u; }
+                }
+            }
+            // wait for this thread's copies in flight (also after a timeout)
+            mbar_wait(bar(4), 0);
+            for (int s2 = 0; s2 < 2; ++s2)
+                if (issued[s2] > 0) mbar_wait(bar(s2), (uint32_t)((issued[s2] - 1) & 1));
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t id_h = idesc_bf16(kTileM, kH), id_o = idesc_bf16(kTileM, kKOUT);
+            uint32_t slot = 0, phase = 0, xph = 0, aph = 0;
+            ok = mbar_wait(bar(4), 0);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                // hidden layers: input buffer X -> A0, H1 -> A1, H2 -> A0
+                for (int layer = 0; layer < 3 && ok; ++layer) {
+                    ok = layer == 0 ? mbar_wait(bar(5), xph) : mbar_wait(bar(6), aph);
+                    if (!ok) break;
+                    if (layer == 0) xph ^= 1u; else aph ^= 1u;
+                    tc_fence_after();
+                    const uint32_t a_base = sbase + (layer == 1 ? kA1 : kA0);
+                    const int kblocks = layer == 0 ? 1 : 4;
+                    for (int kb = 0; kb < kblocks && ok; ++kb) {
+                        ok = mbar_wait(bar(slot), phase);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t b_base = sbase + kRing + slot * kSlot;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            umma(tmem, sdesc(a_base + kb * 16384u + 32u * j), sdesc(b_base + 32u * j), id_h,
+                                 (kb | j) != 0);
+                        umma_commit(bar(2 + slot));
+                        if (++slot == 2) { slot = 0; phase ^= 1u; }
+                    }
+                    umma_commit(bar(7));
+                }
+                if (!ok) break;
+                // output layer: H3 in A1, W4 resident, accumulators at column 256
+                ok = mbar_wait(bar(6), aph);
+                if (!ok) break;
+                aph ^= 1u;
+                tc_fence_after();
+                for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        umma(tmem + 256u, sdesc(sbase + kA1 + kb * 16384u + 32u * j),
+                             sdesc(sbase + kW4 + kb * 4096u + 32u * j), id_o, (kb | j) != 0);
+                umma_commit(bar(8));
+            }
+            // every MMA this thread issued has completed before teardown
+            umma_commit(bar(9));
+            mbar_wait(bar(9), 0);
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int r = 32 * q + lane;                        // row in the tile = tensor-memory lane
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+        uint32_t hph = 0, oph = 0;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t row = t * kTileM + r;
+            const bool valid = row < A.B;
+            // features -> A0, K-block 0 (columns >= n_in are zero); this half writes chunks 4h..4h+3
+            for (int ch = 4 * half; ch < 4 * half + 4; ++ch) {
+                float f[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int c = 8 * ch + i;
+                    f[i] = (valid && c < A.n_in) ? A.x[row * A.n_in + c] : 0.0f;
+                }
+                const uint4 v = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                                           pack_bf16(f[6], f[7]));
+                *reinterpret_cast<uint4 *>(sm + kA0 + sw128_offset(r, 8 * ch, 16384)) = v;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(5));
+            for (int layer = 0; layer < 3 && ok; ++layer) {
+                ok = __all_sync(0xffffffffu, mbar_wait(bar(7), hph));
+                if (!ok) break;
+                hph ^= 1u;
+                tc_fence_after();
+                const float *bias = layer == 0 ? A.b1 : (layer == 1 ? A.b2 : A.b3);
+                uint8_t *out = sm + (layer == 1 ? kA0 : kA1);
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c0 = 128 * half + 32 * cc;
+                    float v[32];
+                    tmem_ld32(lane_addr + (uint32_t)c0, v);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int c = c0 + 8 * g + 2 * i;
+                            w[i] = pack_bf16(gelu_tc(v[8 * g + 2 * i] + __ldg(bias + c)),
+                                             gelu_tc(v[8 * g + 2 * i + 1] + __ldg(bias + c + 1)));
+                        }
+                        *reinterpret_cast<uint4 *>(out + sw128_offset(r, c0 + 8 * g, 16384)) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                tc_fence_before();
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(6));
+            }
+            if (!ok) break;
+            ok = __all_sync(0xffffffffu, mbar_wait(bar(8), oph));
+            if (!ok) break;
+            oph ^= 1u;
+            tc_fence_after();
+            if (half == 0) {
+                float v[32];
+                tmem_ld32(lane_addr + 256u, v);
+                if (valid)
+                    for (int c = 0; c < A.n_out; ++c)
+                        A.y[row * A.n_out + c] = (v[c] + __ldg(A.b4 + c)) * __ldg(A.ystd + c) + __ldg(A.ymean + c);
+            }
+            tc_fence_before();
+        }
+    }
+    if (!ok) {
+        atomicExch(A.err, 1);
+        // rows of this CTA's tiles may be unfinished: mark every output of them
+        if (warp >= 2 && (warp - 2) >> 2 == 0) {
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                const int64_t row = t * kTileM + 32 * (warp & 3) + lane;
+                if (row < A.B)
+                    for (int c = 0; c < A.n_out; ++c) A.y[row * A.n_out + c] = __int_as_float(0x7fc00000);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// Weight image: every layer's [out x in] matrix as BF16 in the 128B-swizzled
+// K-major layout of the kernel's shared memory, K-blocks of 64 columns.
+__global__ void k_mlp_tc_image(const float *p, int64_t o1, int64_t o2, int64_t o3, int64_t o4, bf16 *img) {
+    const int64_t total = (int64_t)kH * kKIN + 2 * (int64_t)kH * kH + (int64_t)kKOUT * kH;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = i, src_off, base;
+        int K, N;
+        if (e < (int64_t)kH * kKIN) { K = kKIN; N = kH; src_off = o1; base = kImgW1; }
+        else if ((e -= (int64_t)kH * kKIN) < (int64_t)kH * kH) { K = kH; N = kH; src_off = o2; base = kImgW2; }
+        else if ((e -= (int64_t)kH * kH) < (int64_t)kH * kH) { K = kH; N = kH; src_off = o3; base = kImgW3; }
+        else { e -= (int64_t)kH * kH; K = kH; N = kKOUT; src_off = o4; base = kImgW4; }
+        const int n = (int)(e / K), k = (int)(e % K);
+        const uint32_t off = sw128_offset(n, k, (uint32_t)N * 128u);
+        img[base + off / 2] = __float2bfloat16(p[src_off + (int64_t)n * K + k]);
+    }
+}
+
+}  // namespace
+
+int mlp_tc_image(mm_ctx *ctx, const float *p, const int64_t oW[4], __nv_bfloat16 *img) {
+    const int64_t total = (int64_t)kH * kKIN + 2 * (int64_t)kH * kH + (int64_t)kKOUT * kH;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+    k_mlp_tc_image<<<blocks, 256, 0, ctx->stream>>>(p, oW[0], oW[1], oW[2], oW[3], img);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int mlp_tc_forward(mm_ctx *ctx, const MlpTcArgs &args) {
+    if (args.B <= 0) return MM_OK;
+    if (kSmemBytes > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "fused MLP needs %u bytes of shared memory", kSmemBytes);
+    MM_CUDA_CHECK(ctx, mm_set_smem(ctx, (const void *)k_mlp_tc, kSmemBytes));
+    const int64_t ntiles = (args.B + kTileM - 1) / kTileM;
+    const int blocks = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms);
+    k_mlp_tc<<<blocks, kThreads, kSmemBytes, ctx->stream>>>(args);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <map>
@@ -23,6 +24,7 @@ struct mm_ctx {
     int ir_max_steps = 4;
     double kappa_max = 0.1;
     int wide64 = 0;     // refinement residuals and projection in native FP64
+    int mlp_layered = 0;   // MLP inference layer by layer (mma.sync) instead of fused (tcgen05)
     // tuned launch shapes of the batched weights kernel, by batch signature
     std::map<std::string, mm_launch_config> tiles;
 };
@@ -79,6 +81,23 @@ struct WeightsJob {
     double *vals[5];  // per operator bit (nullptr if not requested)
     int32_t *status;
 };
+
+// Fused MLP inference on the tensor cores (mlp_tc.cu): x [B x n_in] FP32 ->
+// y [B x n_out] FP32 (denormalised); img is the weight image built by
+// mlp_tc_image from the padded FP32 parameters (oW: offsets of W1..W4).
+struct MlpTcArgs {
+    const float *x;
+    int n_in;
+    int64_t B;
+    const __nv_bfloat16 *img;
+    const float *b1, *b2, *b3, *b4, *ymean, *ystd;
+    int n_out;
+    float *y;
+    int *err;   // set to 1 if a wait timed out (those rows' outputs are NaN)
+};
+constexpr int64_t kMlpTcImageElems = 16384 * 9 + 8192;   // W1 + W2 + W3 + W4 as BF16
+int mlp_tc_image(mm_ctx *ctx, const float *p, const int64_t oW[4], __nv_bfloat16 *img);
+int mlp_tc_forward(mm_ctx *ctx, const MlpTcArgs &args);
 
 int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision);
 // FP32 + refinement kernel of one class (2D / 3D); handed-over rows go to fb_list

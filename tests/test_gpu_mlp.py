@@ -76,6 +76,35 @@ def test_forward_and_gradients_match_oracle(P, ctx, oracle):
     net.close()
 
 
+@pytest.mark.parametrize("B", [1, 127, 128, 300, 5000, 65536 + 129])
+def test_fused_inference_matches_layered(P, ctx, B):
+    """The fused tensor-core forward (tcgen05, one launch for all rows) equals
+    the layer-by-layer forward of the same BF16 network to BF16 rounding, for
+    ragged row counts (partial last tile, more tiles than SMs, more rows than
+    one layered batch)."""
+    net = P.MLP(ctx, N_IN, N_OUT, seed=11)
+    rng = np.random.default_rng(2)
+    p = net.get_params()
+    p += rng.normal(scale=0.02, size=p.shape).astype(np.float32)   # nonzero biases too
+    net.set_params(p)
+    net.set_output_scaling(rng.normal(size=N_OUT), rng.uniform(0.5, 2.0, size=N_OUT))
+    x = torch.from_numpy(rng.uniform(-1, 1, size=(B, N_IN)).astype(np.float32)).cuda()
+    y_f = torch.full((B, N_OUT), float("nan"), device="cuda")
+    y_l = torch.full((B, N_OUT), float("nan"), device="cuda")
+    net.forward(x, y_f)
+    ctx.set_option(P.binding.OPT_MLP_INFER, P.binding.MLP_LAYERED)
+    try:
+        net.forward(x, y_l)
+    finally:
+        ctx.set_option(P.binding.OPT_MLP_INFER, P.binding.MLP_FUSED)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y_f).all()
+    err = (y_f - y_l).abs().max().item()
+    scale = y_l.abs().max().item()
+    assert err <= 2e-2 * scale, (err, scale)
+    net.close()
+
+
 def test_params_and_checkpoint_roundtrip(P, ctx, tmp_path):
     net = P.MLP(ctx, N_IN, N_OUT, seed=5)
     rng = np.random.default_rng(1)
