@@ -814,8 +814,10 @@ def run_surrogate(args, rk):
     w = vals["sur"].view(neval, n).cpu().numpy()
     r = vals["fp64"].view(neval, n).cpu().numpy()
     err = np.abs(w - r).max(1) / np.abs(r).max(1)
-    line = {"metric": METRIC, "value": res["sur"]["value"], "unit": "nodes/s", "n_gpus": rk.world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["sur"]["ms"],
+    # headline: the surrogate with the FP32+IR solve as fallback; the form
+    # whose fallback is the plain FP64 solve is reported beside it
+    line = {"metric": METRIC, "value": res["surir"]["value"], "unit": "nodes/s", "n_gpus": rk.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["surir"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32+f64", "data": "synthetic",
             "config": {"workload": f"surrogate: MLP 50-256x3-25 trained on {ntrain} jittered-patch "
@@ -823,8 +825,9 @@ def run_surrogate(args, rk):
                        "tau": tau},
             "fp64_plain": res["fp64"], "fp32_ir": res["ir"], "surrogate_fp64_fallback": res["sur"],
             "surrogate_fp32ir_fallback": res["surir"],
-            "speedup_vs_fp64_plain": res["fp64"]["ms"] / res["sur"]["ms"],
-            "speedup_fp32ir_fallback_vs_fp32ir": res["ir"]["ms"] / res["surir"]["ms"],
+            "speedup_vs_fp64_plain": res["fp64"]["ms"] / res["surir"]["ms"],
+            "speedup_vs_fp32_ir": res["ir"]["ms"] / res["surir"]["ms"],
+            "speedup_fp64_fallback_vs_fp64_plain": res["fp64"]["ms"] / res["sur"]["ms"],
             "accept_fraction": float(acc.mean()),
             "error_vs_fp64": {"accepted_median": float(np.median(err[acc])) if acc.any() else None,
                               "accepted_p99": float(np.quantile(err[acc], 0.99)) if acc.any() else None,

@@ -471,19 +471,19 @@ struct ProjParams {
 };
 
 __device__ __forceinline__ float phs32(float r2, int k) {
-    float p = sqrtf(r2);
+    float p = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     for (int i = 1; i < k; i += 2) p *= r2;
     return p;
 }
 
 template <int DIM, bool W64>
 __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjParams J) {
-    constexpr int NM = 32, LM = 16, QP = LM + 1, GP = LM + 4;
+    constexpr int NM = 32, LM = 16, QP = LM + 1, GP = LM + 1;   // odd pitches: conflict-free rows
     const WParams &P = J.P;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     __shared__ double s_xi[4][NM * DIM];          // offsets (FP64; double-FP32 in place unless W64)
     __shared__ double s_Q[4][NM][QP];             // Q (double-FP32 pairs, or FP64 if W64)
-    __shared__ __align__(16) float s_G[4][LM][GP]; // Jacobi-scaled Gram matrix, then its inverse
+    __shared__ float s_G[4][LM][GP];              // Jacobi-scaled Gram matrix, then its inverse
     __shared__ float s_A[4][NM][NM + 1];          // FP32 phi matrix for the residual check
     __shared__ double s_w[4][NM];                 // weights (double-FP32 pairs, or FP64 if W64)
     __shared__ float s_u[4][LM], s_d[4][LM], s_z[4][LM], s_r[4][NM];
@@ -638,10 +638,17 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
                     double corr = 0.0;
                     for (int b = 0; b < l; ++b) corr = fma(Qd[lane][b], (double)zz[b], corr);
                     wd[lane] += corr;
-                } else {
+                } else if (pass == 0) {
+                    // the first correction is large: its product with Q is compensated
                     FFAcc acc(wf[lane]);
                     for (int b = 0; b < l; ++b) acc.sub(Qf[lane][b], make_float2(-zz[b], 0.0f));
                     wf[lane] = ff_fast_sum(acc.hi, __fadd_rn(acc.lo, __fadd_rn(acc.la, acc.lb)));
+                } else {
+                    // later ones are small: their FP32 rounding is far below the tolerance
+                    float corr = 0.0f;
+                    for (int b = 0; b < l; ++b) corr = fmaf(Qf[lane][b].x, zz[b], corr);
+                    const float2 t = ff_two_sum(wf[lane].x, corr);
+                    wf[lane] = ff_fast_sum(t.x, __fadd_rn(t.y, wf[lane].y));
                 }
             }
             __syncwarp();
