@@ -313,9 +313,10 @@ class DiskPipeline:
 
 def timed_disk_steps(pipe, precision, steps, stream, flush):
     """Per-step CUDA-event times (L2 flushed between steps): whole step,
-    weights, and the dominant launch (interior weights)."""
+    weights, and the dominant launch (interior weights); the operator
+    applications' times are left in timed_disk_steps.apply_ms."""
     import torch
-    tot, wts, dom = [], [], []
+    tot, wts, dom, app = [], [], [], []
     for _ in range(steps):
         flush.add_(1.0)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -332,10 +333,12 @@ def timed_disk_steps(pipe, precision, steps, stream, flush):
         tot.append(ev[0].elapsed_time(ev[4]))
         wts.append(ev[1].elapsed_time(ev[3]))
         dom.append(ev[1].elapsed_time(ev[2]))
+        app.append(ev[3].elapsed_time(ev[4]))
+    timed_disk_steps.apply_ms = np.array(app)
     return np.array(tot), np.array(wts), np.array(dom)
 
 
-def oracle_rows(ns, rp, col, rows, k, m, ops):
+def oracle_rows(ns, rp, col, rows, k, m, ops, nthreads=None):
     """Oracle weights of arbitrary CSR rows (local renumbering, rows first);
     returns {row: [R, n]}."""
     from oracle import oracle as O
@@ -348,7 +351,7 @@ def oracle_rows(ns, rp, col, rows, k, m, ops):
     lrp = np.zeros(len(rows) + 1, dtype=np.int64)
     np.cumsum([len(s) for s in sts], out=lrp[1:])
     vals, st, _ = O.weights(ns.pts[order], lrp, lcol, k, m, ops, normals=ns.normals[order],
-                            rows=(0, len(rows)), nthreads=O.nthreads_default())
+                            rows=(0, len(rows)), nthreads=nthreads or O.nthreads_default())
     return {int(i): vals[:, lrp[t]:lrp[t + 1]] for t, i in enumerate(rows)}
 
 
@@ -448,10 +451,25 @@ def cpu_baseline_disk(ns, rp, col_h, seconds=15.0, seed=0):
         t0 = time.perf_counter()
         oracle_rows(ns, rp, col_h, rows, spec["k"], spec["m"], spec["ops"])
         t_w += (time.perf_counter() - t0) / len(rows) * share
+    # one thread: a smaller sample of the same mix
+    q1 = rng.choice(np.arange(ib, ie), 32, replace=False)
+    t0 = time.perf_counter()
+    O.knn(ns.pts, 25, queries=q1, nthreads=1)
+    t_knn1 = (time.perf_counter() - t0) / len(q1)
+    t_w1 = 0.0
+    for (b, e), spec, share in (((ib, ie), DISK["interior"], 1 - frac_b),
+                                ((bb, be), DISK["boundary"], frac_b)):
+        rows = np.sort(rng.choice(np.arange(b, e), max(1, int(1000 * share)), replace=False))
+        t0 = time.perf_counter()
+        oracle_rows(ns, rp, col_h, rows, spec["k"], spec["m"], spec["ops"], nthreads=1)
+        t_w1 += (time.perf_counter() - t0) / len(rows) * share
     return {"value": 1.0 / (t_knn + t_w), "unit": "nodes/s", "cores": threads, "kind": "oracle",
             "sample": f"{sk} brute-force kNN queries over all {ns.N} nodes + {sw} weight rows "
                       f"(interior/boundary in proportion), all host cores",
-            "knn_s_per_node": t_knn, "weights_s_per_node": t_w}
+            "knn_s_per_node": t_knn, "weights_s_per_node": t_w,
+            "single_thread": {"value": 1.0 / (t_knn1 + t_w1), "unit": "nodes/s", "cores": 1,
+                              "sample": f"{len(q1)} kNN queries + 1000 weight rows, one thread",
+                              "knn_s_per_node": t_knn1, "weights_s_per_node": t_w1}}
 
 
 def run_disk(args, rk):
@@ -478,6 +496,7 @@ def run_disk(args, rk):
     rk.barrier()
     torch.cuda.synchronize()
     tot, wts, dom = timed_disk_steps(pipe, P.FP32_IR, args.steps, stream, flush)
+    apply_ms = float(np.median(timed_disk_steps.apply_ms))
     torch.cuda.synchronize()
     # the same chosen form with native FP64 refinement residuals (MM_WIDE_FP64)
     ctx.set_option(P.binding.OPT_WIDE, P.binding.WIDE_FP64)
@@ -535,6 +554,16 @@ def run_disk(args, rk):
             "peak_source": "FP32 FMA peak measured in this run (mm_measure_fma_peak); "
                            "MEASURED_PEAKS.json has no FP32 CUDA-core figure"}
     f64_plain = fp64_solve_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
+    # operator application (3 SpMVs, the last with beta = 1): values and column
+    # indices once, row pointers, x and y once per row (algorithmic bytes)
+    N = ns.N
+    spmv_bytes = 3 * (12 * pipe.nnz + 8 * (N + 1) + 16 * N) + 8 * N
+    hbm = peaks_file().get("hbm_gbs")
+    spmv_roof = {"bound": "hbm", "kernel": "k_spmv (3 operator applications per step)",
+                 "achieved": spmv_bytes / (apply_ms * 1e-3) / 1e9, "unit": "GB/s",
+                 "peak": hbm, "frac": (spmv_bytes / (apply_ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                 "bytes": spmv_bytes, "ms": apply_ms,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     # the plain solve's FP64 flops delivered per second by the chosen form
     fp64_equiv = {"tflops": f64_plain / (dom_ms * 1e-3) / 1e12,
                   "frac_of_fp64_peak": f64_plain / (dom_ms * 1e-3) / fp64_peak}
@@ -556,7 +585,7 @@ def run_disk(args, rk):
                                "note": "same form, refinement residuals in native FP64"},
             "fp64_equivalent": fp64_equiv,
             "speedup_vs_fp64_plain": ms64 / ms, "weights_ms": float(np.mean(wts)),
-            "fallback_fraction": fallback, "roofline": roof,
+            "fallback_fraction": fallback, "roofline": roof, "roofline_spmv": spmv_roof,
             "peaks_measured": {"fp64_flops": fp64_peak, "fp32_flops": fp32_peak},
             "e2e": e2e, "clocks": clk, "gpu_launches": DISK_LAUNCHES_PER_STEP * args.steps}
     if rk.rank == 0 and not args.no_error:

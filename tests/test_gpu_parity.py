@@ -244,6 +244,28 @@ def test_mixed_fallback_path_is_exercised(P, ctx, oracle, weight_inputs):
         assert np.array_equal(got[nm], ref64[nm])
 
 
+def test_condition_gate_agrees_with_oracle_kappa(P, ctx, oracle, weight_inputs):
+    """The mixed solver's condition number (||K||_1 times the exact norm of
+    its FP32 inverse) matches the oracle's explicit-inverse kappa_1: with the
+    gate threshold at the median kappa_1 of a sample, the rows clearly above it
+    go to the FP64 solve and the rows clearly below it do not."""
+    ns, rp, col, cls = weight_inputs("disk")
+    b, e, n_max, k, m, ops = cls[0]                      # interior class
+    rng = np.random.default_rng(3)
+    rows = np.sort(rng.choice(np.arange(b, e), 300, replace=False))
+    kap = np.array([oracle.kkt_cond1(ns.pts, col[rp[i]:rp[i + 1]], k, m) for i in rows])
+    med = float(np.median(kap))
+    c2 = P.Context(0)
+    c2.set_option(P.binding.OPT_KAPPA_MAX, med * 2.0 ** -24)
+    got, status = run_gpu_weights(c2, P, ns, rp, col, [cls[0]], P.FP32_IR)
+    c2.close()
+    st = status[rows]
+    hi, lo = kap > 1.1 * med, kap < med / 1.1
+    assert hi.sum() >= 20 and lo.sum() >= 20, (hi.sum(), lo.sum())
+    assert (st[hi] == P.binding.ST_FALLBACK).all(), kap[hi][st[hi] != P.binding.ST_FALLBACK]
+    assert (st[lo] == P.binding.ST_OK).all(), kap[lo][st[lo] != P.binding.ST_OK]
+
+
 def test_bad_rows_get_status_and_zero_weights(P, ctx):
     rng = np.random.default_rng(7)
     pts = rng.uniform(size=(64, 2))
