@@ -57,7 +57,9 @@
 #define ORC_OP_DY 2
 #define ORC_OP_DZ 3
 #define ORC_OP_DN 4
-#define ORC_NOPS 5
+/* second derivatives d^2/dx_a dx_b, bits 5..10: xx, xy, yy, xz, yz, zz */
+#define ORC_OP_DXX 5
+#define ORC_NOPS 11
 
 #define ORC_MAXDIM 3
 #define ORC_MAXDEG 6

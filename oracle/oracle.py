@@ -136,7 +136,7 @@ def knn(pts: np.ndarray, n: int, queries=None, nthreads: int = 1):
 
 
 def op_list(ops: int):
-    return [b for b in range(5) if ops & (1 << b)]
+    return [b for b in range(11) if ops & (1 << b)]
 
 
 def weights(pts, row_ptr, col, k, m, ops, normals=None, rows=None, nthreads: int = 1,

@@ -9,7 +9,14 @@ import itertools
 
 import numpy as np
 
-OPS = [("lap", 1), ("dx", 2), ("dy", 4), ("dz", 8), ("dn", 16)]
+OPS = [("lap", 1), ("dx", 2), ("dy", 4), ("dz", 8), ("dn", 16), ("dxx", 32), ("dxy", 64), ("dyy", 128),
+       ("dxz", 256), ("dyz", 512), ("dzz", 1024)]
+SECOND = {"dxx": (0, 0), "dxy": (0, 1), "dyy": (1, 1), "dxz": (0, 2), "dyz": (1, 2), "dzz": (2, 2)}
+
+
+def op_order(name):
+    """Derivative order q of an operator (weights scale by s^-q)."""
+    return 2 if name == "lap" or name in SECOND else 1
 
 
 def op_names(ops):
@@ -29,6 +36,13 @@ def lop(e, name, normal):
         return 2.0 if (e.sum() == 2 and e.max() == 2) else 0.0
     if name == "dn":
         return float(sum(normal[a] for a in range(len(e)) if e.sum() == 1 and e[a] == 1))
+    if name in SECOND:
+        a, b = SECOND[name]
+        if e.sum() != 2:
+            return 0.0
+        if a == b:
+            return 2.0 if e[a] == 2 else 0.0
+        return 1.0 if (e[a] == 1 and e[b] == 1) else 0.0
     a = {"dx": 0, "dy": 1, "dz": 2}[name]
     return 1.0 if (e.sum() == 1 and e[a] == 1) else 0.0
 
@@ -48,7 +62,7 @@ def monomial_residual(pts, normals, row_ptr, col, w, name, m, rows):
     weights w; operator order q rescales them by s^q)."""
     dim = pts.shape[1]
     E = exps_graded(dim, m)
-    q = 2 if name == "lap" else 1
+    q = op_order(name)
     worst = 0.0
     for i in rows:
         a, b = row_ptr[i], row_ptr[i + 1]

@@ -28,14 +28,27 @@ def exps_graded(dim, m):
 
 
 def lop_monomial(e, op, normal=None):
-    """Operator applied to x^e at the origin (Laplacian, d/dx_a, d/dn)."""
+    """Operator applied to x^e at the origin (Laplacian, d/dx_a, d/dn,
+    d2/dx_a dx_b): the derivative of x^e is nonzero at 0 only for the one
+    monomial whose exponents match the derivative orders."""
     e = np.asarray(e)
     if op == "lap":
         return 2.0 if (e.sum() == 2 and e.max() == 2) else 0.0
     if op == "dn":
         return float(sum(normal[a] for a in range(len(e)) if e.sum() == 1 and e[a] == 1))
+    if len(op) == 3:                                 # dxx, dxy, ... : d/dx_a d/dx_b
+        a, b = "xyz".index(op[1]), "xyz".index(op[2])
+        want = np.zeros(len(e), dtype=int)
+        want[a] += 1
+        want[b] += 1
+        return float(math.factorial(want[a]) * (1 if a == b else math.factorial(want[b]))) \
+            if np.array_equal(e, want) else 0.0
     a = {"dx": 0, "dy": 1, "dz": 2}[op]
     return 1.0 if (e.sum() == 1 and e[a] == 1) else 0.0
+
+
+OPNAMES = [("lap", 1), ("dx", 2), ("dy", 4), ("dz", 8), ("dn", 16), ("dxx", 32), ("dxy", 64), ("dyy", 128),
+           ("dxz", 256), ("dyz", 512), ("dzz", 1024)]
 
 
 def random_stencils(ns, n, count, seed, oracle):
@@ -151,7 +164,8 @@ def load_closed_forms():
     return cases
 
 
-OPBIT = {"lap": 1, "dx": 2, "dy": 4, "dz": 8}
+OPBIT = {"lap": 1, "dx": 2, "dy": 4, "dz": 8, "dxx": 32, "dxy": 64, "dyy": 128, "dxz": 256, "dyz": 512,
+         "dzz": 1024}
 
 
 @pytest.mark.parametrize("case", load_closed_forms(), ids=lambda c: c["name"] + "_" + c["op"])
@@ -182,7 +196,7 @@ def test_monomial_reproduction(oracle, cfg):
     ns = {"square": lambda: NS.square(0.02), "disk": lambda: NS.disk_holes(15000, seed=3),
           "ball": lambda: NS.ball(20000, seed=4)}[kind]()
     dim = ns.dim
-    ops = 1 | 2 | 4 | (8 if dim == 3 else 0) | 16
+    ops = 1 | 2 | 4 | (8 if dim == 3 else 0) | 16 | 32 | 64 | 128 | ((256 | 512 | 1024) if dim == 3 else 0)
     rng = np.random.default_rng(5)
     normals = rng.normal(size=ns.pts.shape)
     normals /= np.linalg.norm(normals, axis=1, keepdims=True)
@@ -201,7 +215,7 @@ def test_monomial_reproduction(oracle, cfg):
                                             rows=(0, rows), scaled=True)
     assert (st == 0).all()
     E = exps_graded(dim, m)
-    names = [o for o, b in [("lap", 1), ("dx", 2), ("dy", 4), ("dz", 8), ("dn", 16)] if ops & b]
+    names = [o for o, b in OPNAMES if ops & b]
     for r in range(rows):
         xi, s = scaled_offsets(P, col[r])
         assert abs(s - scale[r]) <= 1e-15 * s
@@ -213,7 +227,7 @@ def test_monomial_reproduction(oracle, cfg):
             resid = np.abs(terms.sum(0) - lq) / np.maximum(1.0, np.abs(terms).sum(0))
             assert resid.max() <= 1e-12, (name, resid.max())
             # unscaled weights = scaled / s^q
-            q = 2 if name == "lap" else 1
+            q = 1 if name in ("dx", "dy", "dz", "dn") else 2
             assert np.allclose(vals[oi, r * n:(r + 1) * n] * s ** q, ws, rtol=1e-13, atol=0)
         # zero row sums of every derivative operator
         for oi in range(len(names)):
@@ -258,6 +272,13 @@ def fd_operator(s, dim, op, normal, delta):
                 e = np.zeros(dim); e[a] = dl
                 acc += (s(z + e)[0] - 2 * s(z)[0] + s(z - e)[0]) / dl ** 2
             return acc
+        if len(op) == 3:                             # d2/dx_a dx_b
+            a, b = "xyz".index(op[1]), "xyz".index(op[2])
+            ea = np.zeros(dim); ea[a] = dl
+            eb = np.zeros(dim); eb[b] = dl
+            if a == b:
+                return (s(z + ea)[0] - 2 * s(z)[0] + s(z - ea)[0]) / dl ** 2
+            return (s(z + ea + eb)[0] - s(z + ea - eb)[0] - s(z - ea + eb)[0] + s(z - ea - eb)[0]) / (4 * dl ** 2)
         direc = np.zeros(dim)
         if op == "dn":
             direc = np.asarray(normal, float)
@@ -283,8 +304,8 @@ def test_weights_differentiate_the_interpolant(oracle, cfg):
     normal = rng.normal(size=dim)
     normal /= np.linalg.norm(normal)
     nrm = np.tile(normal, (n, 1))
-    ops = 1 | 2 | 4 | (8 if dim == 3 else 0) | 16
-    names = [o for o, b in [("lap", 1), ("dx", 2), ("dy", 4), ("dz", 8), ("dn", 16)] if ops & b]
+    ops = 1 | 2 | 4 | (8 if dim == 3 else 0) | 16 | 32 | 64 | 128 | ((256 | 512 | 1024) if dim == 3 else 0)
+    names = [o for o, b in OPNAMES if ops & b]
     vals, st, scale, svals = oracle.weights(pts, one_row_csr(pts), np.arange(n, dtype=np.int32),
                                             k, m, ops, normals=nrm, rows=(0, 1), scaled=True)
     assert st[0] == 0
