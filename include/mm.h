@@ -55,6 +55,14 @@ extern "C" {
 #define MM_DY 4u    /* d/dy                                        */
 #define MM_DZ 8u    /* d/dz (dim 3)                                */
 #define MM_DN 16u   /* d/dn = sum_a n_a d/dx_a with the node normal */
+/* second derivatives d2/dx_a dx_b (z ones need dim 3); the batched call
+ * (mm_rbffd_weights_batched) takes at most 5 operator bits per class */
+#define MM_DXX 32u
+#define MM_DXY 64u
+#define MM_DYY 128u
+#define MM_DXZ 256u
+#define MM_DYZ 512u
+#define MM_DZZ 1024u
 
 /* ------------------------------------------------------------ precisions */
 #define MM_FP64 0     /* plain FP64 solve                                      */
@@ -152,9 +160,12 @@ typedef struct {
  *     [A Q; Q^T 0] [w; lambda] = [l_phi; l_q],
  *     A_ij = ||xi_i - xi_j||^k, Q_ib = q_b(xi_i),
  * l_phi, l_q = the operator applied to each basis function at xi = 0; the
- * stored weights are w / s^q (q = 2 for MM_LAP, 1 for first derivatives).
+ * stored weights are w / s^q (q = 2 for MM_LAP and second derivatives, 1 for
+ * first derivatives).
  *
- *   ops        bitmask of MM_LAP | MM_DX | MM_DY | MM_DZ | MM_DN.
+ *   ops        bitmask of MM_LAP | MM_DX | MM_DY | MM_DZ | MM_DN and the
+ *              second derivatives MM_DXX .. MM_DZZ (these need m >= 2); more
+ *              than 5 bits are computed in launches of at most 5 columns.
  *   k, m       odd k in {3, 5, 7}; 0 <= m <= 6; l = C(m + dim, dim).
  *   d_pts      [N x dim] nodes; d_normals [N x dim] unit normals (needed
  *              only with MM_DN; may be NULL otherwise).

@@ -18,6 +18,7 @@ from . import _build
 MM_OK, MM_EBADARG, MM_ENOMEM, MM_ECUDA, MM_EUNSUPPORTED = 0, -1, -2, -3, -4
 ST_OK, ST_SINGULAR, ST_NONCONVERGED, ST_FALLBACK, ST_BADARG, ST_DUPLICATE, ST_ACCEPTED = range(7)
 LAP, DX, DY, DZ, DN = 1, 2, 4, 8, 16
+DXX, DXY, DYY, DXZ, DYZ, DZZ = 32, 64, 128, 256, 512, 1024
 FP64, FP32_IR = 0, 1
 KNN_AUTO, KNN_BRUTE, KNN_GRID = 0, 1, 2
 OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX, OPT_WIDE, OPT_MLP_INFER = 1, 2, 3, 4, 5

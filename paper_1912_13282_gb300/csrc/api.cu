@@ -66,8 +66,11 @@ int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int6
                           const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
                           int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job) {
     if (bad_dim(dim)) return mm_fail(ctx, MM_EBADARG, "dim must be 2 or 3");
-    if (ops == 0 || ops >= 32u) return mm_fail(ctx, MM_EBADARG, "ops must be a nonzero MM_* bitmask");
-    if ((ops & MM_DZ) && dim != 3) return mm_fail(ctx, MM_EBADARG, "MM_DZ needs dim 3");
+    if (ops == 0 || ops >= 2048u) return mm_fail(ctx, MM_EBADARG, "ops must be a nonzero MM_* bitmask");
+    if ((ops & (MM_DZ | MM_DXZ | MM_DYZ | MM_DZZ)) && dim != 3)
+        return mm_fail(ctx, MM_EBADARG, "z derivatives need dim 3");
+    if ((ops & (MM_DXX | MM_DXY | MM_DYY | MM_DXZ | MM_DYZ | MM_DZZ)) && m < 2)
+        return mm_fail(ctx, MM_EBADARG, "second derivatives need monomials of degree >= 2");
     if ((ops & MM_DN) && !d_normals) return mm_fail(ctx, MM_EBADARG, "MM_DN needs d_normals");
     if (k != 3 && k != 5 && k != 7) return mm_fail(ctx, MM_EBADARG, "k must be 3, 5 or 7");
     if (m < 0 || m > 6) return mm_fail(ctx, MM_EBADARG, "m must be in [0, 6]");
@@ -94,7 +97,7 @@ int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int6
     J.n_max = n_max;
     J.status = d_status;
     int r = 0;
-    for (int b = 0; b < 5; ++b) {
+    for (int b = 0; b < 11; ++b) {
         J.vals[b] = nullptr;
         if (ops & (1u << b)) {
             if (!d_vals[r]) return mm_fail(ctx, MM_EBADARG, "d_vals[%d] is NULL", r);

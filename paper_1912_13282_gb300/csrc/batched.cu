@@ -185,6 +185,8 @@ int prepare(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int prec
     jobs.clear();
     for (int i = 0; i < nclasses; ++i) {
         const mm_weights_class &C = classes[i];
+        if (__builtin_popcount(C.ops) > 5)
+            return mm_fail(ctx, MM_EUNSUPPORTED, "class %d: at most 5 operator bits per class", i);
         WeightsJob job{};
         int rc = weights_job_from_args(ctx, C.ops, C.k, C.m, C.dim, C.N, C.d_pts, C.d_normals,
                                        &C.stencils, C.row_begin, C.row_end, C.n_max, C.d_vals,

@@ -78,7 +78,7 @@ struct WeightsJob {
     const int32_t *col;
     int64_t row_begin, row_end;
     int n_max;
-    double *vals[5];  // per operator bit (nullptr if not requested)
+    double *vals[11];  // per operator bit (nullptr if not requested)
     int32_t *status;
 };
 

@@ -35,6 +35,23 @@ int rbffd_init_device(mm_ctx *ctx) {
 // workspace.
 int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, int *fb_count,
                            int *fb_list) {
+    if (__builtin_popcount(job.ops) > 5) {
+        // more than 5 operators: launches of at most 5 right-hand-side columns
+        // each, in bit order (the factorization is repeated per launch; a
+        // row's status is the last launch's)
+        unsigned rest = job.ops;
+        while (rest) {
+            unsigned part = 0;
+            for (int b = 0, c = 0; b < 11 && c < 5; ++b)
+                if (rest & (1u << b)) { part |= 1u << b; ++c; }
+            WeightsJob sub = job;
+            sub.ops = part;
+            const int rc = weights_launch_scratch(ctx, sub, precision, fb_count, fb_list);
+            if (rc != MM_OK) return rc;
+            rest &= ~part;
+        }
+        return MM_OK;
+    }
     const int dim = job.dim;
     WParams P = wparams_from_job(ctx, job);
     if (P.M_max > kMaxM) return mm_fail(ctx, MM_EUNSUPPORTED, "n_max + l = %d > %d", P.M_max, kMaxM);

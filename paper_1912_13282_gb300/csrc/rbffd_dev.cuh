@@ -29,8 +29,29 @@ struct MonoTable {
     signed char var[2][kMaxMono];
     signed char lap[2][kMaxMono];   // Laplacian of q_b at 0 (0 or 2)
     signed char lin[2][kMaxMono];   // a if q_b = xi_a, else -1
+    signed char d2[2][kMaxMono];    // for degree-2 q_b = xi_a xi_c (a <= c): 3a + c, else -1
 };
+
 __constant__ MonoTable c_mono;
+
+// second-derivative operator code (5..10) -> index pair (a, c), a <= c
+__host__ __device__ inline int d2_a(int op) { return op == 5 || op == 6 || op == 8 ? 0 : (op == 7 || op == 9 ? 1 : 2); }
+__host__ __device__ inline int d2_c(int op) { return op == 5 ? 0 : (op == 6 || op == 7 ? 1 : 2); }
+// d2/dxi_a dxi_c of monomial b at 0: 2 for xi_a^2, 1 for xi_a xi_c (a != c), 0 otherwise
+__device__ inline int d2_of_monomial(int di, int b, int op) {
+    const int a = d2_a(op), c = d2_c(op);
+    return c_mono.d2[di][b] == 3 * a + c ? (a == c ? 2 : 1) : 0;
+}
+// derivative order of an operator column (the weights unscale by s^-order)
+__host__ __device__ inline int op_order(int op) { return op == 0 || op >= 5 ? 2 : 1; }
+// d2/dx_a dx_c of ||x - xi_j||^k at the centre, from r^2 = ||xi_j||^2 and
+// rk2 = r^(k-2): k r^(k-2) delta_ac + k (k-2) r^(k-4) xi_a xi_c (0 at r = 0)
+__device__ inline double phs_d2(int op, int k, double r2, double rk2, const double *x) {
+    const int a = d2_a(op), c = d2_c(op);
+    double v = a == c ? (double)k * rk2 : 0.0;
+    if (r2 > 0.0) v += (double)(k * (k - 2)) * (rk2 / r2) * x[a] * x[c];
+    return v;
+}
 
 struct WParams {
     int dim, k, m, l, R;
@@ -42,7 +63,8 @@ struct WParams {
     const int32_t *col;
     int64_t row_begin, row_end;
     double *vals[5];           // per right-hand-side column
-    int opcode[5];             // operator bit index per column (0 LAP, 1..3 d/dx_a, 4 d/dn)
+    int opcode[5];             // operator bit index per column (0 LAP, 1..3 d/dx_a, 4 d/dn,
+                               // 5..10 d2/dx_a dx_b: xx, xy, yy, xz, yz, zz)
     int32_t *status;
     // mixed-path controls
     int *fb_list;              // rows queued for the FP64 solve
@@ -203,6 +225,8 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
             double v;
             if (op == 0) {
                 v = (double)(k * (k + DIM - 2)) * rk2;
+            } else if (op >= 5) {
+                v = phs_d2(op, k, r2, rk2, xi + j * DIM);
             } else {
                 double dot;
                 if (op == 4) {
@@ -223,6 +247,8 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
             double v = 0.0;
             if (op == 0) {
                 v = (double)c_mono.lap[di][b];
+            } else if (op >= 5) {
+                v = (double)d2_of_monomial(di, b, op);
             } else {
                 int a = c_mono.lin[di][b];
                 if (a >= 0) {
@@ -244,7 +270,7 @@ __device__ void store_weights(const WParams &P, int64_t rb, int n, double s, con
     const int lane = threadIdx.x & 31;
     double inv_s = 1.0 / s;
     for (int cI = 0; cI < P.R; ++cI) {
-        double sc = P.opcode[cI] == 0 ? inv_s * inv_s : inv_s;
+        double sc = op_order(P.opcode[cI]) == 2 ? inv_s * inv_s : inv_s;
         double *out = P.vals[cI] + rb;
         for (int j = lane; j < n; j += 32) out[j] = (double)X[j * xp + col0 + cI] * sc;
     }
@@ -672,6 +698,23 @@ __device__ __forceinline__ float2 ff_phs_km2(float2 r2, int k) {
     for (int i = 3; i < k; i += 2) v = ff_mul(v, r2);
     return v;
 }
+// 1/a by one Newton correction of the FP32 reciprocal (a != 0)
+__device__ __forceinline__ float2 ff_recip(float2 a) {
+    const float h = __frcp_rn(a.x);
+    const float e = __fsub_rn(fmaf(-a.x, h, 1.0f), __fmul_rn(a.y, h));   // 1 - a h
+    return ff_fast_sum(h, __fmul_rn(h, e));
+}
+// the double-FP32 counterpart of phs_d2 (xf: this node's offsets)
+__device__ inline float2 ff_phs_d2(int op, int k, float2 r2, float2 rk2, const float2 *xf) {
+    const int a = d2_a(op), c = d2_c(op);
+    float2 v = a == c ? ff_scale(rk2, (float)k) : make_float2(0.0f, 0.0f);
+    if (r2.x > 0.0f) {
+        // r^(k-4): r^-1 for k = 3, else r (r^2)^((k-5)/2)
+        const float2 rk4 = k == 3 ? ff_recip(ff_sqrt(r2)) : ff_phs_km2(r2, k - 2);
+        v = ff_add(v, ff_scale(ff_mul(rk4, ff_mul(xf[a], xf[c])), (float)(k * (k - 2))));
+    }
+    return v;
+}
 
 // The system for the residuals in double-FP32: A [n x pA] (diagonal 0), Q
 // [n x l], B [M x R] (rows < n: l_phi, rows n + b: l_q), from the scaled
@@ -719,6 +762,8 @@ __device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int 
                 v = make_float2(0.0f, 0.0f);      // unused solver column
             } else if (op == 0) {
                 v = ff_scale(rk2, (float)(k * (k + DIM - 2)));
+            } else if (op >= 5) {
+                v = ff_phs_d2(op, k, r2, rk2, xf + r * DIM);
             } else {
                 float2 dot;
                 if (op == 4) {
@@ -741,6 +786,8 @@ __device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int 
             if (cI < P.R) {
                 if (op == 0) {
                     v.x = (float)c_mono.lap[di][b];
+                } else if (op >= 5) {
+                    v.x = (float)d2_of_monomial(di, b, op);
                 } else {
                     const int a = c_mono.lin[di][b];
                     if (a >= 0) v = op == 4 ? ff_from_double(P.normals[row * DIM + a])
@@ -800,6 +847,8 @@ __device__ __noinline__ float assemble_f64(const WParams &P, int64_t row, int n,
                 v = 0.0;                  // unused solver column
             } else if (op == 0) {
                 v = (double)(k * (k + DIM - 2)) * rk2;
+            } else if (op >= 5) {
+                v = phs_d2(op, k, r2, rk2, xi + r * DIM);
             } else {
                 double dot;
                 if (op == 4) {
@@ -821,6 +870,8 @@ __device__ __noinline__ float assemble_f64(const WParams &P, int64_t row, int n,
             if (cI < P.R) {
                 if (op == 0) {
                     v = (double)c_mono.lap[di][b];
+                } else if (op >= 5) {
+                    v = (double)d2_of_monomial(di, b, op);
                 } else {
                     const int a = c_mono.lin[di][b];
                     if (a >= 0) v = op == 4 ? P.normals[row * DIM + a] : ((a == op - 1) ? 1.0 : 0.0);
@@ -1089,7 +1140,7 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
     // unscaled store
     const double inv_s = 1.0 / s;
     for (int cI = 0; cI < P.R; ++cI) {
-        const double sc = P.opcode[cI] == 0 ? inv_s * inv_s : inv_s;
+        const double sc = op_order(P.opcode[cI]) == 2 ? inv_s * inv_s : inv_s;
         double *out = P.vals[cI] + rb;
         if (P.wide64) {
             const double *X = (const double *)(base + Ly.x64);
@@ -1123,7 +1174,7 @@ inline WParams wparams_from_job(const mm_ctx *ctx, const WeightsJob &job) {
     P.row_end = job.row_end;
     P.status = job.status;
     int R = 0;
-    for (int b = 0; b < 5; ++b)
+    for (int b = 0; b < 11 && R < 5; ++b)      // callers pass at most 5 operator bits
         if (job.ops & (1u << b)) {
             P.vals[R] = job.vals[b];
             P.opcode[R] = b;
@@ -1179,10 +1230,18 @@ void mono_table_host(MonoTable &t) {
             }
             t.lap[di][b] = (deg == 2 && twos == 1) ? 2 : 0;
             t.lin[di][b] = (deg == 1 && ones == 1) ? (signed char)which : -1;
+            t.d2[di][b] = -1;
+            if (deg == 2) {
+                int a0 = -1, a1 = -1;
+                for (int a = 0; a < 3; ++a)
+                    for (int r = 0; r < exps[b][a]; ++r) (a0 < 0 ? a0 : a1) = a;
+                t.d2[di][b] = (signed char)(3 * a0 + a1);
+            }
         }
         for (int b = cnt; b < kMaxMono; ++b) {
             t.parent[di][b] = t.var[di][b] = t.lap[di][b] = 0;
             t.lin[di][b] = -1;
+            t.d2[di][b] = -1;
         }
     }
 }

@@ -163,6 +163,17 @@ def weight_case(name):
     if name == "square":
         ns = NS.square(0.01)
         spec = [("all", 12, 3, 2, 1 | 2 | 4)]
+    elif name == "square_d2":
+        # all 2D operators (6 columns: two launches of at most 5), r^3 and r^5
+        ns = NS.square(0.02)
+        spec = [("all", 12, 3, 2, 1 | 2 | 4 | 32 | 64 | 128)]
+    elif name == "disk_d2":
+        ns = NS.disk_holes(20000, seed=5)
+        spec = [("interior", 25, 5, 4, 32 | 64 | 128), ("boundary", 30, 5, 4, 16 | 32 | 128)]
+    elif name == "ball_d2":
+        ns = NS.ball(15000, seed=6)
+        spec = [("interior", 35, 3, 2, 32 | 64 | 128 | 256 | 512 | 1024), ("refined", 60, 3, 3, 1 | 256 | 1024),
+                ("boundary", 45, 3, 2, 16 | 32)]
     elif name == "disk":
         ns = NS.disk_holes(20000, seed=5)
         spec = [("interior", 25, 5, 4, 1 | 2 | 4), ("boundary", 30, 5, 4, 16)]
@@ -193,7 +204,7 @@ def weight_inputs(P, ctx):
     return get
 
 
-@pytest.mark.parametrize("name", ["square", "disk", "ball"])
+@pytest.mark.parametrize("name", ["square", "disk", "ball", "square_d2", "disk_d2", "ball_d2"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_ir", "fp32_ir_wide64"])
 def test_weights_match_oracle(P, ctx, oracle, weight_inputs, name, precision):
     """fp32_ir refines with double-FP32 residuals (the default), fp32_ir_wide64
