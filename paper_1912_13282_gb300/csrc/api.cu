@@ -25,6 +25,20 @@ int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...) {
     return code;
 }
 
+int mm_warps_per_block(const mm_ctx *ctx, size_t bytes_per_warp, int max_wpb) {
+    int best = 1, best_warps = 0;
+    for (int w = 1; w <= max_wpb; ++w) {
+        const size_t blk = bytes_per_warp * (size_t)w;
+        if (blk > ctx->smem_optin) break;
+        const int blocks = (int)std::min<size_t>(32 / w, ctx->smem_per_sm / (blk + ctx->smem_reserved));
+        if (blocks * w >= best_warps) {
+            best_warps = blocks * w;
+            best = w;
+        }
+    }
+    return best;
+}
+
 char *mm_workspace(mm_ctx *ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return ctx->ws;
     size_t want = bytes + bytes / 4 + (1 << 20);
@@ -124,13 +138,17 @@ int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream) {
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     DeviceGuard g(ctx);
-    int sms = 0, optin = 0;
+    int sms = 0, optin = 0, per_sm = 0, reserved = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess) {
         delete ctx;
         return MM_ECUDA;
     }
     ctx->num_sms = sms;
+    ctx->smem_per_sm = (size_t)per_sm;
+    ctx->smem_reserved = (size_t)reserved;
     ctx->smem_optin = (size_t)optin;
     if (rbffd_init_device(ctx) != MM_OK || batched_init_device(ctx) != MM_OK ||
         mlp_init_device(ctx) != MM_OK || mixed_init_device_2d(ctx) != MM_OK ||

@@ -15,7 +15,9 @@ struct mm_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     int num_sms = 0;
-    size_t smem_optin = 0;
+    size_t smem_optin = 0;          // largest dynamic shared memory per block
+    size_t smem_per_sm = 0;         // shared memory per SM
+    size_t smem_reserved = 0;       // shared memory the system reserves per block
     // growable device workspace (bump-allocated per call)
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -36,6 +38,10 @@ int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...);
 // what was set before for this kernel on this device (so launches inside a
 // stream capture make no attribute call once warmed up).
 cudaError_t mm_set_smem(const mm_ctx *ctx, const void *kernel, size_t bytes);
+
+// Warps per block (1 .. max_wpb) that fit the most warps on an SM when each
+// warp needs `bytes_per_warp` of shared memory.
+int mm_warps_per_block(const mm_ctx *ctx, size_t bytes_per_warp, int max_wpb);
 
 // Ensures the workspace holds at least `bytes`; returns its base or nullptr.
 char *mm_workspace(mm_ctx *ctx, size_t bytes);
