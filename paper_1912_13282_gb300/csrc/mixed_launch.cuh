@@ -28,7 +28,7 @@ template <int DIM, int RPL, int R>
 int launch_mixed_t(mm_ctx *ctx, const WParams &P, int64_t rows) {
     const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
     auto kern = k_weights_mixed<DIM, RPL, R>;
-    const int wpb = mm_warps_per_block(ctx, Ly.bytes, 4);
+    const int wpb = mm_warps_per_block(ctx, (const void *)kern, Ly.bytes, 4);
     const size_t sm = Ly.bytes * wpb;
     if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "stencil too large for shared memory");
     MM_CUDA_CHECK(ctx, mm_set_smem(ctx, (const void *)kern, sm));

@@ -1127,7 +1127,11 @@ int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, 
     F.list_count = cnt;
     if (fallback_precision == MM_FP32_IR) {
         const MixedLayout Ly = mixed_layout(P.n_max, P.l, 1, dim);
-        const int mw = mm_warps_per_block(ctx, Ly.bytes, 4);
+        const int rpl0 = (P.M_max + 31) / 32;
+        const void *mk0 = rpl0 <= 1 ? (const void *)k_surrogate_fallback_mixed<2, 1>
+                                    : (rpl0 == 2 ? (const void *)k_surrogate_fallback_mixed<2, 2>
+                                                 : (const void *)k_surrogate_fallback_mixed<2, 3>);
+        const int mw = mm_warps_per_block(ctx, mk0, Ly.bytes, 4);
         const size_t msm = Ly.bytes * mw;
         const int rpl = (P.M_max + 31) / 32;
         const void *mk = rpl <= 1 ? (const void *)k_surrogate_fallback_mixed<2, 1>

@@ -39,9 +39,10 @@ int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...);
 // stream capture make no attribute call once warmed up).
 cudaError_t mm_set_smem(const mm_ctx *ctx, const void *kernel, size_t bytes);
 
-// Warps per block (1 .. max_wpb) that fit the most warps on an SM when each
-// warp needs `bytes_per_warp` of shared memory.
-int mm_warps_per_block(const mm_ctx *ctx, size_t bytes_per_warp, int max_wpb);
+// Warps per block (1 .. max_wpb) that keep the most warps of `kernel`
+// resident on an SM when each warp needs `bytes_per_warp` of dynamic shared
+// memory (the kernel's shared-memory attribute is raised as needed).
+int mm_warps_per_block(const mm_ctx *ctx, const void *kernel, size_t bytes_per_warp, int max_wpb);
 
 // Ensures the workspace holds at least `bytes`; returns its base or nullptr.
 char *mm_workspace(mm_ctx *ctx, size_t bytes);
