@@ -802,7 +802,7 @@ def run_surrogate(args, rk):
     t_data = time.time() - t0
     net = P.MLP(ctx, 2 * n, n, seed=rk.rank)
     t0 = time.time()
-    losses = S.train(net, data["x"], data["t"], epochs=20, batch=4096, lr=3e-3, lr_final=1e-4)
+    losses = S.train(net, data["x"], data["t"], epochs=120, batch=4096, lr=3e-3, lr_final=1e-4)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del data
@@ -849,7 +849,7 @@ def run_surrogate(args, rk):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["surir"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32+f64", "data": "synthetic",
-            "config": {"workload": f"surrogate: MLP 50-256x3-25 trained on {ntrain} jittered-patch "
+            "config": {"workload": f"surrogate: MLP 50-256x3-25 trained (120 epochs) on {ntrain} jittered-patch "
                                    f"stencils, {neval} held-out stencils (n=25, r^5, deg 4)",
                        "tau": tau},
             "fp64_plain": res["fp64"], "fp32_ir": res["ir"], "surrogate_fp64_fallback": res["sur"],
