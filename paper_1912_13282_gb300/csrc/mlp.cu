@@ -460,8 +460,9 @@ __global__ void k_features(const double *pts, const int64_t *rp, const int32_t *
 // context asks for native FP64 (MM_OPT_WIDE); z comes from an FP32
 // inverse of the Jacobi-scaled Gram matrix (in-place Gauss-Jordan, no
 // pivoting: the matrix is symmetric positive definite).
-// Residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r (least
-// squares), rho = ||r - Q lambda||_inf / ||l_phi||_inf; accept if rho <= tau.
+// Residual check (FP32, A evaluated on the fly): r = l_phi - A w, lambda =
+// (Q^T Q)^-1 Q^T r (least squares), rho = ||r - Q lambda||_inf /
+// ||l_phi||_inf; accept if rho <= tau.  Up to 8 blocks of 4 warps per SM.
 struct ProjParams {
     WParams P;              // LAP only, k, m, row range, output vals[0]
     const float *wt;        // [rows x n] predictions (scaled units), row - row_begin
@@ -477,20 +478,18 @@ __device__ __forceinline__ float phs32(float r2, int k) {
 }
 
 template <int DIM, bool W64>
-__global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjParams J) {
+__global__ void __launch_bounds__(128, 8) k_project(const __grid_constant__ ProjParams J) {
     constexpr int NM = 32, LM = 16, QP = LM + 1, GP = LM + 1;   // odd pitches: conflict-free rows
     const WParams &P = J.P;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     __shared__ double s_xi[4][NM * DIM];          // offsets (FP64; double-FP32 in place unless W64)
     __shared__ double s_Q[4][NM][QP];             // Q (double-FP32 pairs, or FP64 if W64)
     __shared__ float s_G[4][LM][GP];              // Jacobi-scaled Gram matrix, then its inverse
-    __shared__ float s_A[4][NM][NM + 1];          // FP32 phi matrix for the residual check
     __shared__ double s_w[4][NM];                 // weights (double-FP32 pairs, or FP64 if W64)
     __shared__ float s_u[4][LM], s_d[4][LM], s_z[4][LM], s_r[4][NM];
     float2 (*Qf)[QP] = reinterpret_cast<float2 (*)[QP]>(s_Q[wib]);
     double (*Qd)[QP] = s_Q[wib];
     float (*G)[GP] = s_G[wib];
-    float (*A)[NM + 1] = s_A[wib];
     float2 *wf = reinterpret_cast<float2 *>(s_w[wib]);
     double *wd = s_w[wib];
     float *u = s_u[wib], *dsc = s_d[wib], *zz = s_z[wib], *rr = s_r[wib];
@@ -531,24 +530,6 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
                 wf[lane] = make_float2(J.wt[(row - P.row_begin) * n + lane], 0.0f);
             }
         }
-        // FP32 phi matrix: unordered pairs (r, (r + d) mod n), each once
-        for (int d = 1; d <= n / 2; ++d) {
-            const int cnt = (2 * d == n) ? n / 2 : n;
-            for (int r = lane; r < cnt; r += 32) {
-                int c = r + d;
-                if (c >= n) c -= n;
-                float r2 = 0.0f;
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) {
-                    const float t = x32(r, a) - x32(c, a);
-                    r2 = fmaf(t, t, r2);
-                }
-                const float v = phs32(r2, k);
-                A[r][c] = v;
-                A[c][r] = v;
-            }
-        }
-        if (lane < n) A[lane][lane] = 0.0f;
         __syncwarp();
         // Gram matrix Q^T Q (FP32, upper triangle), Jacobi scaling
         for (int e = lane; e < l * (l + 1) / 2; e += 32) {
@@ -653,35 +634,79 @@ __global__ void __launch_bounds__(128) k_project(const __grid_constant__ ProjPar
             }
             __syncwarp();
         }
-        // residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r, e = r - Q lambda
-        float lphi = 0.0f;
+        // residual check (FP32): r = l_phi - A w, lambda = (Q^T Q)^-1 Q^T r, e = r - Q lambda.
+        // Short dependency chains: w in FP32 staged once, two accumulators per
+        // sum, the multipliers broadcast from shared memory.
+        if (lane < n) rr[lane] = w32(lane);
+        __syncwarp();
+        float lphi = 0.0f, r_own = 0.0f;
         if (lane < n) {
             float r2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < DIM; ++a) r2 = fmaf(x32(lane, a), x32(lane, a), r2);
-            float rk2 = sqrtf(r2);
+            float rk2 = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
             for (int i = 3; i < k; i += 2) rk2 *= r2;
             lphi = (float)(k * (k + DIM - 2)) * rk2;
-            float aw = 0.0f;
-            for (int j = 0; j < n; ++j) aw = fmaf(A[lane][j], w32(j), aw);
-            rr[lane] = lphi - aw;
+            // (A w)_lane with A = phi(||xi_lane - xi_j||) evaluated on the fly
+            float xo[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) xo[a] = x32(lane, a);
+            float a0 = 0.0f, a1 = 0.0f;
+            int j = 0;
+            auto phi_w = [&](int jj) {
+                float d2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    const float t = xo[a] - x32(jj, a);
+                    d2 = fmaf(t, t, d2);
+                }
+                return phs32(d2, k) * rr[jj];
+            };
+            for (; j + 1 < n; j += 2) {
+                a0 += phi_w(j);
+                a1 += phi_w(j + 1);
+            }
+            if (j < n) a0 += phi_w(j);
+            r_own = lphi - (a0 + a1);
         }
         __syncwarp();
-        float qr = 0.0f;
-        if (bl < l)
-            for (int j = j0; j < j1; ++j) qr = fmaf(q32(j, bl), rr[j], qr);
-        qr += __shfl_xor_sync(kFull, qr, 16);
-        const float dq = bl < l ? qr * dsc[bl] : 0.0f;
-        float lam = 0.0f;
-        for (int a = 0; a < l; ++a) lam = fmaf(G[bl < l ? bl : 0][a], __shfl_sync(kFull, dq, a), lam);
+        if (lane < n) rr[lane] = r_own;
         __syncwarp();
-        if (lane < l) zz[lane] = lam * dsc[lane];
+        float q0 = 0.0f, q1 = 0.0f;
+        if (bl < l) {
+            int j = j0;
+            for (; j + 1 < j1; j += 2) {
+                q0 = fmaf(q32(j, bl), rr[j], q0);
+                q1 = fmaf(q32(j + 1, bl), rr[j + 1], q1);
+            }
+            if (j < j1) q0 = fmaf(q32(j, bl), rr[j], q0);
+        }
+        float qr = q0 + q1;
+        qr += __shfl_xor_sync(kFull, qr, 16);
+        if (bl < l && hl == 0) u[bl] = qr * dsc[bl];
+        __syncwarp();
+        if (lane < l) {
+            float l0 = 0.0f, l1 = 0.0f, l2 = 0.0f;
+            int a = 0;
+            for (; a + 2 < l; a += 3) {
+                l0 = fmaf(G[lane][a], u[a], l0);
+                l1 = fmaf(G[lane][a + 1], u[a + 1], l1);
+                l2 = fmaf(G[lane][a + 2], u[a + 2], l2);
+            }
+            for (; a < l; ++a) l0 = fmaf(G[lane][a], u[a], l0);
+            zz[lane] = (l0 + l1 + l2) * dsc[lane];
+        }
         __syncwarp();
         float e = 0.0f;
         if (lane < n) {
-            float ql = 0.0f;
-            for (int b = 0; b < l; ++b) ql = fmaf(q32(lane, b), zz[b], ql);
-            e = fabsf(rr[lane] - ql);
+            float e0 = 0.0f, e1 = 0.0f;
+            int b = 0;
+            for (; b + 1 < l; b += 2) {
+                e0 = fmaf(q32(lane, b), zz[b], e0);
+                e1 = fmaf(q32(lane, b + 1), zz[b + 1], e1);
+            }
+            if (b < l) e0 = fmaf(q32(lane, b), zz[b], e0);
+            e = fabsf(r_own - (e0 + e1));
         }
         float emax = e, lmax = fabsf(lphi);
         for (int o = 16; o; o >>= 1) {
