@@ -90,6 +90,11 @@ extern "C" {
 #define MM_OPT_MLP_INFER 5     /* MLP inference (mm_mlp_forward, surrogate):    */
 #define MM_MLP_FUSED 0         /*   one fused tensor-core kernel (default)     */
 #define MM_MLP_LAYERED 1       /*   layer-by-layer GEMMs (the training path)   */
+#define MM_OPT_GJ 6            /* storage of the FP32 Gauss-Jordan inverse:     */
+#define MM_GJ_AUTO 0           /*   rows in registers for systems of 33..48    */
+                               /*   unknowns (M_max rounded up to 40 or 48),   */
+                               /*   shared memory otherwise (default)          */
+#define MM_GJ_SHARED 1         /*   shared memory for every size (same result) */
 
 typedef struct mm_ctx mm_ctx;
 

@@ -21,9 +21,10 @@ LAP, DX, DY, DZ, DN = 1, 2, 4, 8, 16
 DXX, DXY, DYY, DXZ, DYZ, DZZ = 32, 64, 128, 256, 512, 1024
 FP64, FP32_IR = 0, 1
 KNN_AUTO, KNN_BRUTE, KNN_GRID = 0, 1, 2
-OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX, OPT_WIDE, OPT_MLP_INFER = 1, 2, 3, 4, 5
+OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX, OPT_WIDE, OPT_MLP_INFER, OPT_GJ = 1, 2, 3, 4, 5, 6
 WIDE_FF, WIDE_FP64 = 0, 1
 MLP_FUSED, MLP_LAYERED = 0, 1
+GJ_AUTO, GJ_SHARED = 0, 1
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",

@@ -222,6 +222,11 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value) {
                 return mm_fail(ctx, MM_EBADARG, "MLP inference must be MM_MLP_FUSED or MM_MLP_LAYERED");
             ctx->mlp_layered = value == MM_MLP_LAYERED;
             return MM_OK;
+        case MM_OPT_GJ:
+            if (value != MM_GJ_AUTO && value != MM_GJ_SHARED)
+                return mm_fail(ctx, MM_EBADARG, "Gauss-Jordan storage must be MM_GJ_AUTO or MM_GJ_SHARED");
+            ctx->gj_shared = value == MM_GJ_SHARED;
+            return MM_OK;
     }
     return mm_fail(ctx, MM_EBADARG, "unknown option %d", key);
 }

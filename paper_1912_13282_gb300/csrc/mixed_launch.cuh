@@ -6,8 +6,10 @@
 
 namespace {
 
-template <int DIM, int RPL, int R>
-__global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
+// The register-resident inverse (W > 0) is held to 168 registers, which
+// keeps three blocks of four warps per SM (the shared-memory limit).
+template <int DIM, int RPL, int R, int W>
+__global__ void __launch_bounds__(128, W > 0 ? 3 : 1) k_weights_mixed(WParams P) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
@@ -15,7 +17,7 @@ __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t row = P.row_begin + gw; row < P.row_end; row += nw) {
-        if (mixed_row<DIM, RPL, R>(P, row, base) && lane == 0) {
+        if (mixed_row<DIM, RPL, R, W>(P, row, base) && lane == 0) {
             const int slot = atomicAdd(P.fb_count, 1);
             P.fb_list[slot] = (int)row;
         }
@@ -24,10 +26,10 @@ __global__ void __launch_bounds__(128) k_weights_mixed(WParams P) {
 }
 
 
-template <int DIM, int RPL, int R>
+template <int DIM, int RPL, int R, int W>
 int launch_mixed_t(mm_ctx *ctx, const WParams &P, int64_t rows) {
     const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
-    auto kern = k_weights_mixed<DIM, RPL, R>;
+    auto kern = k_weights_mixed<DIM, RPL, R, W>;
     const int wpb = mm_warps_per_block(ctx, (const void *)kern, Ly.bytes, 4);
     const size_t sm = Ly.bytes * wpb;
     if (sm > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "stencil too large for shared memory");
@@ -38,22 +40,30 @@ int launch_mixed_t(mm_ctx *ctx, const WParams &P, int64_t rows) {
     return MM_OK;
 }
 
-template <int DIM, int RPL>
+template <int DIM, int RPL, int W = 0>
 int launch_mixed_r(mm_ctx *ctx, const WParams &P, int64_t rows) {
     switch (P.R) {
-        case 1: return launch_mixed_t<DIM, RPL, 1>(ctx, P, rows);
-        case 2: return launch_mixed_t<DIM, RPL, 2>(ctx, P, rows);
-        case 3: return launch_mixed_t<DIM, RPL, 3>(ctx, P, rows);
-        case 4: return launch_mixed_t<DIM, RPL, 4>(ctx, P, rows);
-        default: return launch_mixed_t<DIM, RPL, 5>(ctx, P, rows);
+        case 1: return launch_mixed_t<DIM, RPL, 1, W>(ctx, P, rows);
+        case 2: return launch_mixed_t<DIM, RPL, 2, W>(ctx, P, rows);
+        case 3: return launch_mixed_t<DIM, RPL, 3, W>(ctx, P, rows);
+        case 4: return launch_mixed_t<DIM, RPL, 4, W>(ctx, P, rows);
+        default: return launch_mixed_t<DIM, RPL, 5, W>(ctx, P, rows);
     }
 }
 
+// Systems of 33..48 unknowns (two rows per lane) invert with the rows in
+// registers (40 or 48 columns); other sizes, or MM_GJ_SHARED, use the
+// shared-memory form.
 template <int DIM>
 int launch_mixed(mm_ctx *ctx, const WParams &P, int64_t rows) {
     const int rpl = (P.M_max + 31) / 32;
+    const int w4 = 4 * ((P.M_max + 3) / 4);
     if (rpl <= 1) return launch_mixed_r<DIM, 1>(ctx, P, rows);
-    if (rpl == 2) return launch_mixed_r<DIM, 2>(ctx, P, rows);
+    if (rpl == 2) {
+        if (!ctx->gj_shared && w4 == 40) return launch_mixed_r<DIM, 2, 40>(ctx, P, rows);
+        if (!ctx->gj_shared && w4 == 48) return launch_mixed_r<DIM, 2, 48>(ctx, P, rows);
+        return launch_mixed_r<DIM, 2>(ctx, P, rows);
+    }
     return launch_mixed_r<DIM, 3>(ctx, P, rows);
 }
 

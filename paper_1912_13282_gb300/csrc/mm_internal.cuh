@@ -27,6 +27,7 @@ struct mm_ctx {
     double kappa_max = 0.1;
     int wide64 = 0;     // refinement residuals and projection in native FP64
     int mlp_layered = 0;   // MLP inference layer by layer (mma.sync) instead of fused (tcgen05)
+    int gj_shared = 0;     // FP32 inverse in shared memory for every system size
     // tuned launch shapes of the batched weights kernel, by batch signature
     std::map<std::string, mm_launch_config> tiles;
 };

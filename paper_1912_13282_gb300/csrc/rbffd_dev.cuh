@@ -561,6 +561,235 @@ __device__ __forceinline__ bool gj32_invert(float *__restrict__ S, int p32, int 
     return ok;
 }
 
+// The same elimination with each lane's rows held in registers (W = 4 *
+// ceil(M_max / 4) columns, rows lane + 32 q).  Every pass shifts the rows left
+// by the number of columns it eliminates and appends the new inverse columns
+// at the right, so the pivot columns are always registers 0 and 1 and every
+// register index is static; after M steps the inverse sits in columns
+// W - M .. W - 1 in step order and is written back to S in the layout the
+// shared-memory form leaves.  Only the two pivot rows pass through shared
+// memory (buf: 4 W floats, 16-byte aligned: raw pivot rows, then the scaled
+// ones).  Each entry sees the same operations in the same order as above,
+// so the two forms give identical inverses.
+template <int RPL, int W>
+__device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, int M, int *step, int *perm,
+                                                float *__restrict__ buf, float tiny) {
+    static_assert(W % 4 == 0 && W <= 32 * RPL, "register width");
+    constexpr int W2 = W / 2, WC4 = W / 4;
+    const int lane = threadIdx.x & 31;
+    const int C4 = (M + 3) >> 2;
+    float *__restrict__ P1 = buf;
+    float *__restrict__ P2 = buf + W;
+    float *__restrict__ U = buf + 2 * W;
+    float *__restrict__ V = buf + 3 * W;
+    const float2 zero2 = make_float2(0.0f, 0.0f);
+    float2 Rw[RPL][W2];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+        const float4 *src = reinterpret_cast<const float4 *>(S + (r < M ? r : 0) * p32);
+#pragma unroll
+        for (int c4 = 0; c4 < WC4; ++c4) {
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (r < M && c4 < C4) a = src[c4];
+            Rw[q][2 * c4] = make_float2(a.x, a.y);
+            Rw[q][2 * c4 + 1] = make_float2(a.z, a.w);
+        }
+    }
+    // raw row q of this lane to dst (W floats)
+    auto put_row = [&](int qs, float *dst) {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (q == qs) {
+                float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+                for (int c4 = 0; c4 < WC4; ++c4)
+                    d4[c4] = make_float4(Rw[q][2 * c4].x, Rw[q][2 * c4].y, Rw[q][2 * c4 + 1].x,
+                                         Rw[q][2 * c4 + 1].y);
+            }
+    };
+    bool ok = true;
+    int kk = 0;
+    for (; kk + 1 < M; kk += 2) {
+        // first pivot: column kk (register 0)
+        unsigned key = 0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (step[q] == kBig) key = max(key, pivot_key(Rw[q][0].x, lane + 32 * q));
+        int p1 = pivot_row(key);
+        if (p1 == kBig) p1 = 0;                    // only when every row is exhausted (not reached)
+        const int o1 = p1 & 31, q1 = p1 >> 5;
+        float2 h1 = Rw[0][0];
+#pragma unroll
+        for (int q = 1; q < RPL; ++q)
+            if (q == q1) h1 = Rw[q][0];
+        const float piv1 = __shfl_sync(kFull, h1.x, o1);
+        const float p1c1 = __shfl_sync(kFull, h1.y, o1);
+        const bool good1 = fabsf(piv1) > tiny;
+        const float ip1 = good1 ? __frcp_rn(piv1) : 0.0f;
+        const float u1n = p1c1 * ip1;              // u1 at column kk+1
+        // own rows: multiplier of step 1 and column kk+1 after step 1
+        float m1[RPL], c1[RPL];
+        unsigned key2 = 0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            m1[q] = Rw[q][0].x;
+            c1[q] = fmaf(-m1[q], u1n, Rw[q][0].y);
+            if (r == p1) step[q] = kk;
+            else if (r < M && step[q] == kBig) key2 = max(key2, pivot_key(c1[q], r));
+        }
+        // second pivot: column kk+1 after step 1
+        int p2 = pivot_row(key2);
+        if (p2 == kBig) p2 = p1 == 0 ? 1 : 0;      // not reached
+        const int o2 = p2 & 31, q2 = p2 >> 5;
+        float m1o = m1[0], c1o = c1[0];
+#pragma unroll
+        for (int q = 1; q < RPL; ++q)
+            if (q == q2) {
+                m1o = m1[q];
+                c1o = c1[q];
+            }
+        const float m1p2 = __shfl_sync(kFull, m1o, o2);
+        const float piv2 = __shfl_sync(kFull, c1o, o2);
+        const bool good2 = fabsf(piv2) > tiny;
+        ok &= good1 && good2;
+        const float ip2 = good2 ? __frcp_rn(piv2) : 0.0f;
+        const float u2k = -m1p2 * ip1 * ip2;       // u2 at column kk
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (lane + 32 * q == p2) step[q] = kk + 1;
+        if (lane == o1) put_row(q1, P1);
+        if (lane == o2) put_row(q2, P2);
+        if (lane == 0) {
+            perm[kk] = p1;
+            perm[kk + 1] = p2;
+        }
+        __syncwarp();
+        // the two scaled pivot rows in the shifted frame, with the new inverse
+        // columns (u1: ip1, 0; u2: u2k, ip2) appended
+        for (int c = lane; c < W; c += 32) {
+            float u, v;
+            if (c < W - 2) {
+                const float a1 = P1[c + 2], a2 = P2[c + 2];
+                u = a1 * ip1;
+                v = fmaf(-m1p2, u, a2) * ip2;
+            } else if (c == W - 2) {
+                u = ip1;
+                v = u2k;
+            } else {
+                u = 0.0f;
+                v = ip2;
+            }
+            U[c] = u;
+            V[c] = v;
+        }
+        __syncwarp();
+        // row <- a * row + b1 * u1 + b2 * u2, shifted by two: other rows take
+        // both rank-1 updates (a = 1), row p1 becomes u1 - u1n u2, row p2 u2
+        float2 al[RPL], b1[RPL], b2[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            const bool live = r < M && r != p1 && r != p2;
+            const float a = live ? 1.0f : 0.0f;
+            const float x1 = live ? -m1[q] : (r == p1 ? 1.0f : 0.0f);
+            const float x2 = live ? -c1[q] : (r == p1 ? -u1n : (r == p2 ? 1.0f : 0.0f));
+            al[q] = make_float2(a, a);
+            b1[q] = make_float2(x1, x1);
+            b2[q] = make_float2(x2, x2);
+        }
+        const float4 *U4 = reinterpret_cast<const float4 *>(U);
+        const float4 *V4 = reinterpret_cast<const float4 *>(V);
+#pragma unroll
+        for (int c4 = 0; c4 < WC4; ++c4) {
+            const float4 u = U4[c4], v = V4[c4];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const float2 o0 = Rw[q][2 * c4 + 1];
+                const float2 o1v = 2 * c4 + 2 < W2 ? Rw[q][2 * c4 + 2] : zero2;
+                float2 lo = ffma2(al[q], o0, zero2);
+                float2 hi = ffma2(al[q], o1v, zero2);
+                lo = ffma2(b1[q], make_float2(u.x, u.y), lo);
+                hi = ffma2(b1[q], make_float2(u.z, u.w), hi);
+                Rw[q][2 * c4] = ffma2(b2[q], make_float2(v.x, v.y), lo);
+                Rw[q][2 * c4 + 1] = ffma2(b2[q], make_float2(v.z, v.w), hi);
+            }
+        }
+    }
+    if (kk < M) {
+        // last column of an odd-sized system: one rank-1 step, shift by one
+        unsigned key = 0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            if (step[q] == kBig) key = max(key, pivot_key(Rw[q][0].x, lane + 32 * q));
+        int p1 = pivot_row(key);
+        if (p1 == kBig) p1 = 0;
+        const int o1 = p1 & 31, q1 = p1 >> 5;
+        float h = Rw[0][0].x;
+#pragma unroll
+        for (int q = 1; q < RPL; ++q)
+            if (q == q1) h = Rw[q][0].x;
+        const float piv = __shfl_sync(kFull, h, o1);
+        const bool good = fabsf(piv) > tiny;
+        ok &= good;
+        const float ip = good ? __frcp_rn(piv) : 0.0f;
+        float2 al[RPL], bb[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = lane + 32 * q;
+            const bool live = r < M && r != p1;
+            const float a = live ? 1.0f : 0.0f;
+            const float x = live ? -Rw[q][0].x : (r == p1 ? 1.0f : 0.0f);
+            al[q] = make_float2(a, a);
+            bb[q] = make_float2(x, x);
+            if (r == p1) step[q] = kk;
+        }
+        if (lane == o1) put_row(q1, P1);
+        if (lane == 0) perm[kk] = p1;
+        __syncwarp();
+        for (int c = lane; c < W; c += 32) U[c] = c < W - 1 ? P1[c + 1] * ip : ip;
+        __syncwarp();
+        const float4 *U4 = reinterpret_cast<const float4 *>(U);
+#pragma unroll
+        for (int c4 = 0; c4 < WC4; ++c4) {
+            const float4 u = U4[c4];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const float2 o0 = make_float2(Rw[q][2 * c4].y, Rw[q][2 * c4 + 1].x);
+                const float2 o1v =
+                    make_float2(Rw[q][2 * c4 + 1].y, 2 * c4 + 2 < W2 ? Rw[q][2 * c4 + 2].x : 0.0f);
+                Rw[q][2 * c4] = ffma2(bb[q], make_float2(u.x, u.y), ffma2(al[q], o0, zero2));
+                Rw[q][2 * c4 + 1] = ffma2(bb[q], make_float2(u.z, u.w), ffma2(al[q], o1v, zero2));
+            }
+        }
+    }
+    // the inverse: columns W - M .. W - 1 of the registers -> columns 0 .. M-1 of S
+    const int off = W - M;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int r = lane + 32 * q;
+        if (r < M) {
+            float *dst = S + r * p32;
+            if (off == 0) {
+                float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+                for (int c4 = 0; c4 < WC4; ++c4)
+                    d4[c4] = make_float4(Rw[q][2 * c4].x, Rw[q][2 * c4].y, Rw[q][2 * c4 + 1].x,
+                                         Rw[q][2 * c4 + 1].y);
+            } else {
+#pragma unroll
+                for (int j = 0; j < W2; ++j) {
+                    if (2 * j >= off) dst[2 * j - off] = Rw[q][j].x;
+                    if (2 * j + 1 >= off) dst[2 * j + 1 - off] = Rw[q][j].y;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    return ok;
+}
+
 // x = K^-1 b for R right-hand sides with the inverse above.  V [M x R]
 // (shared, natural row order) holds b on entry and x on exit; Bp [4*ceil(M/4)
 // x R] (shared, 16-byte aligned) is scratch for b in pivot order.
@@ -637,6 +866,9 @@ __host__ __device__ inline MixedLayout mixed_layout(int n_max, int l, int R, int
     L.u32 = take((size_t)2 * 4 * C4 * 4);
     L.v32 = take((size_t)M * R * 4);
     L.bp = take((size_t)4 * C4 * R * 4);
+    // u32 .. bp double as the 4 * (4 C4) floats of the register-resident
+    // inverse's scratch (v32 and bp are used only after the inverse)
+    if (o - L.u32 < (size_t)4 * 4 * C4 * 4) o = L.u32 + (size_t)4 * 4 * C4 * 4;
     L.perm = take((size_t)M * 4);
     L.bytes = o;
     return L;
@@ -1029,7 +1261,8 @@ __device__ __forceinline__ bool mixed_refine(const WParams &P, int n, int M, con
 // symmetric, so both norms agree); a stencil with ||K|| ||K^-1|| u32 above
 // the bound goes to the FP64 solver.  The refinement (mixed_refine) keeps K,
 // b and x in double-FP32 with compensated residuals, or in FP64 (P.wide64).
-template <int DIM, int RPL, int R>
+// W > 0 (= 4 ceil(M_max / 4)) selects the register-resident inverse.
+template <int DIM, int RPL, int R, int W = 0>
 __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base) {
     const int lane = threadIdx.x & 31;
     const MixedLayout Ly = mixed_layout(P.n_max, P.l, R, DIM);
@@ -1106,7 +1339,11 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
         }
     }
     n1 = warp_maxf(n1);
-    bool queue = !gj32_invert<RPL>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
+    bool queue;
+    if constexpr (W > 0)
+        queue = !gj32_invert_reg<RPL, W>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
+    else
+        queue = !gj32_invert<RPL>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
     if (!queue) {
         float ninv = 0.0f;
 #pragma unroll

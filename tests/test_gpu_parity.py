@@ -255,6 +255,63 @@ def test_mixed_fallback_path_is_exercised(P, ctx, oracle, weight_inputs):
         assert np.array_equal(got[nm], ref64[nm])
 
 
+@pytest.mark.parametrize("name", ["disk", "ball", "disk_d2"])
+def test_register_and_shared_inverse_agree_bitwise(P, ctx, weight_inputs, name):
+    """Systems of 33..48 unknowns invert with each lane's rows in registers
+    (disk interior M = 40, disk boundary and ball interior M = 45); the
+    shared-memory form performs the same operations in the same order, so
+    weights and statuses are identical."""
+    ns, rp, col, cls = weight_inputs(name)
+    got, st = run_gpu_weights(ctx, P, ns, rp, col, cls, P.FP32_IR)
+    c2 = P.Context(0)
+    c2.set_option(P.binding.OPT_GJ, P.binding.GJ_SHARED)
+    ref, st2 = run_gpu_weights(c2, P, ns, rp, col, cls, P.FP32_IR)
+    c2.close()
+    assert np.array_equal(st, st2)
+    for nm in got:
+        assert np.array_equal(got[nm], ref[nm]), nm
+
+
+def test_register_inverse_ragged_stencils(P, ctx, oracle, weight_inputs):
+    """Rows of 20..25 nodes in a class of n_max = 25 (M = 35..40 in a
+    40-column register frame: the inverse lands 0..5 columns from the left
+    edge) and a few rows of odd M: identical to the shared-memory form and
+    within 1e-7 of the oracle."""
+    ns, rp, col, cls = weight_inputs("disk")
+    b, e = ns.classes["interior"]
+    rows = np.arange(b, b + 6000)
+    n_i = 20 + (rows % 6)
+    sizes = np.zeros(ns.N, dtype=np.int64)          # rows outside the range stay empty
+    sizes[rows] = n_i
+    rp2 = np.zeros(ns.N + 1, dtype=np.int64)
+    np.cumsum(sizes, out=rp2[1:])
+    col2 = np.concatenate([col[rp[i]:rp[i] + n] for i, n in zip(rows, n_i)]).astype(np.int32)
+    pts_d, rp_d, col_d = dev(ns.pts), dev(rp2), dev(col2)
+    out = []
+    for form in (P.binding.GJ_AUTO, P.binding.GJ_SHARED):
+        c = P.Context(0)
+        c.set_option(P.binding.OPT_GJ, form)
+        vals = [torch.zeros(len(col2), dtype=torch.float64, device="cuda") for _ in range(3)]
+        st = torch.full((ns.N,), -1, dtype=torch.int32, device="cuda")
+        c.rbffd_weights(1 | 2 | 4, 5, 4, pts_d, rp_d, col_d, vals, row_begin=int(rows[0]),
+                        row_end=int(rows[-1]) + 1, n_max=25, precision=P.FP32_IR, status=st)
+        torch.cuda.synchronize()
+        out.append(([v.cpu().numpy() for v in vals], st.cpu().numpy()[rows]))
+        c.close()
+    (w_reg, st_reg), (w_sh, st_sh) = out
+    assert np.array_equal(st_reg, st_sh) and set(np.unique(st_reg)) <= {0, P.binding.ST_FALLBACK}
+    for a, r in zip(w_reg, w_sh):
+        assert np.array_equal(a, r)
+    sample = rows[::7]
+    ref = oracle_rows(oracle, ns.pts, ns.normals, rp2, col2, sample, 5, 4, 1 | 2 | 4)
+    for oi in range(3):
+        w_ref = np.zeros_like(w_reg[oi])
+        for i in sample:
+            w_ref[rp2[i]:rp2[i + 1]] = ref[int(i)][oi]
+        err = rel_err_rows(w_reg[oi], w_ref, rp2, sample)
+        assert err.max() <= 1e-7, (oi, err.max())
+
+
 def test_condition_gate_agrees_with_oracle_kappa(P, ctx, oracle, weight_inputs):
     """The mixed solver's condition number (||K||_1 times the exact norm of
     its FP32 inverse) matches the oracle's explicit-inverse kappa_1: with the
