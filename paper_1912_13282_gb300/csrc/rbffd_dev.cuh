@@ -561,106 +561,108 @@ __device__ __forceinline__ bool gj32_invert(float *__restrict__ S, int p32, int 
     return ok;
 }
 
-// The same elimination with each lane's rows held in registers (W = 4 *
-// ceil(M_max / 4) columns, rows lane + 32 q).  Every pass shifts the rows left
-// by the number of columns it eliminates and appends the new inverse columns
-// at the right, so the pivot columns are always registers 0 and 1 and every
-// register index is static; after M steps the inverse sits in columns
-// W - M .. W - 1 in step order and is written back to S in the layout the
-// shared-memory form leaves.  Only the two pivot rows pass through shared
-// memory (buf: 4 W floats, 16-byte aligned: raw pivot rows, then the scaled
-// ones).  Each entry sees the same operations in the same order as above,
-// so the two forms give identical inverses.
-template <int RPL, int W>
+// The same elimination with the rows held in registers, for systems of
+// 33..W unknowns (W = 40 or 48 = 4 ceil(M_max / 4)).  Lane L holds row L in
+// full and one of PARTS = 32 / (W - 32) consecutive pieces (PC = W / PARTS
+// columns) of row 32 + L / PARTS, so the second rows cost every lane PC
+// columns instead of W.  Every pass shifts the rows left by the number of
+// columns it eliminates and appends the new inverse columns at the right,
+// so the pivot columns are always registers 0 and 1 and every register index
+// is static; a piece's last columns come from the next piece by a shuffle.
+// After M steps the inverse sits in columns W - M .. W - 1 in step order and
+// is written back to S in the layout the shared-memory form leaves.  Only
+// the pivot rows pass through shared memory (buf: 4 W floats, 16-byte
+// aligned: the raw pivot rows, then the scaled ones).  Each entry sees the
+// same operations in the same order as the shared-memory form, so the two
+// give identical inverses.
+template <int W>
 __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, int M, int *step, int *perm,
                                                 float *__restrict__ buf, float tiny) {
-    static_assert(W % 4 == 0 && W <= 32 * RPL, "register width");
+    static_assert(W == 40 || W == 48, "register width");
     constexpr int W2 = W / 2, WC4 = W / 4;
+    constexpr int PARTS = 32 / (W - 32), PC = W / PARTS, PC2 = PC / 2;
     const int lane = threadIdx.x & 31;
-    const int C4 = (M + 3) >> 2;
+    const int C4 = (M + 3) >> 2, W4 = 4 * C4;
+    const int pt = lane % PARTS, r1 = 32 + lane / PARTS, c1base = pt * PC;
+    const int lead = lane - pt;                // lane holding columns 0.. of row r1
+    const bool last = pt == PARTS - 1;
     float *__restrict__ P1 = buf;
     float *__restrict__ P2 = buf + W;
     float *__restrict__ U = buf + 2 * W;
     float *__restrict__ V = buf + 3 * W;
     const float2 zero2 = make_float2(0.0f, 0.0f);
-    float2 Rw[RPL][W2];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int r = lane + 32 * q;
-        const float4 *src = reinterpret_cast<const float4 *>(S + (r < M ? r : 0) * p32);
+    float2 A0[W2];                             // row lane
+    float2 A1[PC2];                            // columns c1base .. c1base + PC - 1 of row r1
+    int st0 = step[0];
+    int st1 = r1 < M ? kBig : -1;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(S + (lane < M ? lane : 0) * p32);
 #pragma unroll
         for (int c4 = 0; c4 < WC4; ++c4) {
             float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (r < M && c4 < C4) a = src[c4];
-            Rw[q][2 * c4] = make_float2(a.x, a.y);
-            Rw[q][2 * c4 + 1] = make_float2(a.z, a.w);
+            if (lane < M && c4 < C4) a = src[c4];
+            A0[2 * c4] = make_float2(a.x, a.y);
+            A0[2 * c4 + 1] = make_float2(a.z, a.w);
         }
-    }
-    // raw row q of this lane to dst (W floats)
-    auto put_row = [&](int qs, float *dst) {
+        const float2 *src1 = reinterpret_cast<const float2 *>(S + (r1 < M ? r1 : 0) * p32 + c1base);
 #pragma unroll
-        for (int q = 0; q < RPL; ++q)
-            if (q == qs) {
+        for (int j = 0; j < PC2; ++j) A1[j] = (r1 < M && c1base + 2 * j < W4) ? src1[j] : zero2;
+    }
+    // the raw pivot row p to dst (W floats): one lane for p < 32, the PARTS
+    // lanes of the row otherwise
+    auto put_row = [&](int p, float *dst) {
+        if (p < 32) {
+            if (lane == p) {
                 float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll
                 for (int c4 = 0; c4 < WC4; ++c4)
-                    d4[c4] = make_float4(Rw[q][2 * c4].x, Rw[q][2 * c4].y, Rw[q][2 * c4 + 1].x,
-                                         Rw[q][2 * c4 + 1].y);
+                    d4[c4] = make_float4(A0[2 * c4].x, A0[2 * c4].y, A0[2 * c4 + 1].x, A0[2 * c4 + 1].y);
             }
+        } else if (r1 == p) {
+            float2 *d2 = reinterpret_cast<float2 *>(dst + c1base);
+#pragma unroll
+            for (int j = 0; j < PC2; ++j) d2[j] = A1[j];
+        }
     };
+    auto lead_of = [](int p) { return p < 32 ? p : (p - 32) * PARTS; };
     bool ok = true;
     int kk = 0;
     for (; kk + 1 < M; kk += 2) {
         // first pivot: column kk (register 0)
         unsigned key = 0;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-            if (step[q] == kBig) key = max(key, pivot_key(Rw[q][0].x, lane + 32 * q));
+        if (st0 == kBig) key = pivot_key(A0[0].x, lane);
+        if (pt == 0 && st1 == kBig) key = max(key, pivot_key(A1[0].x, r1));
         int p1 = pivot_row(key);
         if (p1 == kBig) p1 = 0;                    // only when every row is exhausted (not reached)
-        const int o1 = p1 & 31, q1 = p1 >> 5;
-        float2 h1 = Rw[0][0];
-#pragma unroll
-        for (int q = 1; q < RPL; ++q)
-            if (q == q1) h1 = Rw[q][0];
-        const float piv1 = __shfl_sync(kFull, h1.x, o1);
-        const float p1c1 = __shfl_sync(kFull, h1.y, o1);
+        const float2 h1 = p1 < 32 ? A0[0] : A1[0];
+        const float piv1 = __shfl_sync(kFull, h1.x, lead_of(p1));
+        const float p1c1 = __shfl_sync(kFull, h1.y, lead_of(p1));
         const bool good1 = fabsf(piv1) > tiny;
         const float ip1 = good1 ? __frcp_rn(piv1) : 0.0f;
         const float u1n = p1c1 * ip1;              // u1 at column kk+1
-        // own rows: multiplier of step 1 and column kk+1 after step 1
-        float m1[RPL], c1[RPL];
+        // multiplier of step 1 and column kk+1 after step 1 (row r1's from its lead lane)
+        const float m10 = A0[0].x, c10 = fmaf(-m10, u1n, A0[0].y);
+        float m11 = A1[0].x, c11 = fmaf(-m11, u1n, A1[0].y);
+        m11 = __shfl_sync(kFull, m11, lead);
+        c11 = __shfl_sync(kFull, c11, lead);
         unsigned key2 = 0;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            const int r = lane + 32 * q;
-            m1[q] = Rw[q][0].x;
-            c1[q] = fmaf(-m1[q], u1n, Rw[q][0].y);
-            if (r == p1) step[q] = kk;
-            else if (r < M && step[q] == kBig) key2 = max(key2, pivot_key(c1[q], r));
-        }
+        if (lane == p1) st0 = kk;
+        else if (lane < M && st0 == kBig) key2 = pivot_key(c10, lane);
+        if (r1 == p1) st1 = kk;
+        else if (pt == 0 && r1 < M && st1 == kBig) key2 = max(key2, pivot_key(c11, r1));
         // second pivot: column kk+1 after step 1
         int p2 = pivot_row(key2);
         if (p2 == kBig) p2 = p1 == 0 ? 1 : 0;      // not reached
-        const int o2 = p2 & 31, q2 = p2 >> 5;
-        float m1o = m1[0], c1o = c1[0];
-#pragma unroll
-        for (int q = 1; q < RPL; ++q)
-            if (q == q2) {
-                m1o = m1[q];
-                c1o = c1[q];
-            }
-        const float m1p2 = __shfl_sync(kFull, m1o, o2);
-        const float piv2 = __shfl_sync(kFull, c1o, o2);
+        const float m1p2 = __shfl_sync(kFull, p2 < 32 ? m10 : m11, lead_of(p2));
+        const float piv2 = __shfl_sync(kFull, p2 < 32 ? c10 : c11, lead_of(p2));
         const bool good2 = fabsf(piv2) > tiny;
         ok &= good1 && good2;
         const float ip2 = good2 ? __frcp_rn(piv2) : 0.0f;
         const float u2k = -m1p2 * ip1 * ip2;       // u2 at column kk
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-            if (lane + 32 * q == p2) step[q] = kk + 1;
-        if (lane == o1) put_row(q1, P1);
-        if (lane == o2) put_row(q2, P2);
+        if (lane == p2) st0 = kk + 1;
+        if (r1 == p2) st1 = kk + 1;
+        put_row(p1, P1);
+        put_row(p2, P2);
         if (lane == 0) {
             perm[kk] = p1;
             perm[kk + 1] = p2;
@@ -684,108 +686,125 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
             U[c] = u;
             V[c] = v;
         }
-        __syncwarp();
         // row <- a * row + b1 * u1 + b2 * u2, shifted by two: other rows take
         // both rank-1 updates (a = 1), row p1 becomes u1 - u1n u2, row p2 u2
-        float2 al[RPL], b1[RPL], b2[RPL];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            const int r = lane + 32 * q;
+        auto coef = [&](int r, float m, float c, float2 &al, float2 &b1, float2 &b2) {
             const bool live = r < M && r != p1 && r != p2;
             const float a = live ? 1.0f : 0.0f;
-            const float x1 = live ? -m1[q] : (r == p1 ? 1.0f : 0.0f);
-            const float x2 = live ? -c1[q] : (r == p1 ? -u1n : (r == p2 ? 1.0f : 0.0f));
-            al[q] = make_float2(a, a);
-            b1[q] = make_float2(x1, x1);
-            b2[q] = make_float2(x2, x2);
-        }
+            const float x1 = live ? -m : (r == p1 ? 1.0f : 0.0f);
+            const float x2 = live ? -c : (r == p1 ? -u1n : (r == p2 ? 1.0f : 0.0f));
+            al = make_float2(a, a);
+            b1 = make_float2(x1, x1);
+            b2 = make_float2(x2, x2);
+        };
+        float2 al0, b10, b20, al1, b11, b21;
+        coef(lane, m10, c10, al0, b10, b20);
+        coef(r1, m11, c11, al1, b11, b21);
+        // first columns of the next piece (zero past the end of the row)
+        float2 nxt = make_float2(__shfl_down_sync(kFull, A1[0].x, 1), __shfl_down_sync(kFull, A1[0].y, 1));
+        if (last) nxt = zero2;
+        __syncwarp();
         const float4 *U4 = reinterpret_cast<const float4 *>(U);
         const float4 *V4 = reinterpret_cast<const float4 *>(V);
 #pragma unroll
         for (int c4 = 0; c4 < WC4; ++c4) {
             const float4 u = U4[c4], v = V4[c4];
+            const float2 o0 = A0[2 * c4 + 1];
+            const float2 o1v = 2 * c4 + 2 < W2 ? A0[2 * c4 + 2] : zero2;
+            float2 lo = ffma2(al0, o0, zero2);
+            float2 hi = ffma2(al0, o1v, zero2);
+            lo = ffma2(b10, make_float2(u.x, u.y), lo);
+            hi = ffma2(b10, make_float2(u.z, u.w), hi);
+            A0[2 * c4] = ffma2(b20, make_float2(v.x, v.y), lo);
+            A0[2 * c4 + 1] = ffma2(b20, make_float2(v.z, v.w), hi);
+        }
+        const float2 *U2 = reinterpret_cast<const float2 *>(U + c1base);
+        const float2 *V2 = reinterpret_cast<const float2 *>(V + c1base);
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-                const float2 o0 = Rw[q][2 * c4 + 1];
-                const float2 o1v = 2 * c4 + 2 < W2 ? Rw[q][2 * c4 + 2] : zero2;
-                float2 lo = ffma2(al[q], o0, zero2);
-                float2 hi = ffma2(al[q], o1v, zero2);
-                lo = ffma2(b1[q], make_float2(u.x, u.y), lo);
-                hi = ffma2(b1[q], make_float2(u.z, u.w), hi);
-                Rw[q][2 * c4] = ffma2(b2[q], make_float2(v.x, v.y), lo);
-                Rw[q][2 * c4 + 1] = ffma2(b2[q], make_float2(v.z, v.w), hi);
-            }
+        for (int j = 0; j < PC2; ++j) {
+            const float2 o = j + 1 < PC2 ? A1[j + 1] : nxt;
+            const float2 t = ffma2(b11, U2[j], ffma2(al1, o, zero2));
+            A1[j] = ffma2(b21, V2[j], t);
         }
     }
     if (kk < M) {
         // last column of an odd-sized system: one rank-1 step, shift by one
         unsigned key = 0;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q)
-            if (step[q] == kBig) key = max(key, pivot_key(Rw[q][0].x, lane + 32 * q));
+        if (st0 == kBig) key = pivot_key(A0[0].x, lane);
+        if (pt == 0 && st1 == kBig) key = max(key, pivot_key(A1[0].x, r1));
         int p1 = pivot_row(key);
         if (p1 == kBig) p1 = 0;
-        const int o1 = p1 & 31, q1 = p1 >> 5;
-        float h = Rw[0][0].x;
-#pragma unroll
-        for (int q = 1; q < RPL; ++q)
-            if (q == q1) h = Rw[q][0].x;
-        const float piv = __shfl_sync(kFull, h, o1);
+        const float piv = __shfl_sync(kFull, p1 < 32 ? A0[0].x : A1[0].x, lead_of(p1));
         const bool good = fabsf(piv) > tiny;
         ok &= good;
         const float ip = good ? __frcp_rn(piv) : 0.0f;
-        float2 al[RPL], bb[RPL];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            const int r = lane + 32 * q;
+        const float m0 = A0[0].x;
+        const float m1 = __shfl_sync(kFull, A1[0].x, lead);
+        auto coef1 = [&](int r, float m, float2 &al, float2 &bb) {
             const bool live = r < M && r != p1;
             const float a = live ? 1.0f : 0.0f;
-            const float x = live ? -Rw[q][0].x : (r == p1 ? 1.0f : 0.0f);
-            al[q] = make_float2(a, a);
-            bb[q] = make_float2(x, x);
-            if (r == p1) step[q] = kk;
-        }
-        if (lane == o1) put_row(q1, P1);
+            const float x = live ? -m : (r == p1 ? 1.0f : 0.0f);
+            al = make_float2(a, a);
+            bb = make_float2(x, x);
+        };
+        float2 al0, bb0, al1, bb1;
+        coef1(lane, m0, al0, bb0);
+        coef1(r1, m1, al1, bb1);
+        if (lane == p1) st0 = kk;
+        if (r1 == p1) st1 = kk;
+        put_row(p1, P1);
         if (lane == 0) perm[kk] = p1;
         __syncwarp();
         for (int c = lane; c < W; c += 32) U[c] = c < W - 1 ? P1[c + 1] * ip : ip;
+        float nx = __shfl_down_sync(kFull, A1[0].x, 1);
+        if (last) nx = 0.0f;
         __syncwarp();
         const float4 *U4 = reinterpret_cast<const float4 *>(U);
 #pragma unroll
         for (int c4 = 0; c4 < WC4; ++c4) {
             const float4 u = U4[c4];
+            const float2 o0 = make_float2(A0[2 * c4].y, A0[2 * c4 + 1].x);
+            const float2 o1v = make_float2(A0[2 * c4 + 1].y, 2 * c4 + 2 < W2 ? A0[2 * c4 + 2].x : 0.0f);
+            A0[2 * c4] = ffma2(bb0, make_float2(u.x, u.y), ffma2(al0, o0, zero2));
+            A0[2 * c4 + 1] = ffma2(bb0, make_float2(u.z, u.w), ffma2(al0, o1v, zero2));
+        }
+        const float2 *U2 = reinterpret_cast<const float2 *>(U + c1base);
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-                const float2 o0 = make_float2(Rw[q][2 * c4].y, Rw[q][2 * c4 + 1].x);
-                const float2 o1v =
-                    make_float2(Rw[q][2 * c4 + 1].y, 2 * c4 + 2 < W2 ? Rw[q][2 * c4 + 2].x : 0.0f);
-                Rw[q][2 * c4] = ffma2(bb[q], make_float2(u.x, u.y), ffma2(al[q], o0, zero2));
-                Rw[q][2 * c4 + 1] = ffma2(bb[q], make_float2(u.z, u.w), ffma2(al[q], o1v, zero2));
-            }
+        for (int j = 0; j < PC2; ++j) {
+            const float2 o = make_float2(A1[j].y, j + 1 < PC2 ? A1[j + 1].x : nx);
+            A1[j] = ffma2(bb1, U2[j], ffma2(al1, o, zero2));
         }
     }
     // the inverse: columns W - M .. W - 1 of the registers -> columns 0 .. M-1 of S
     const int off = W - M;
+    if (lane < M) {
+        float *dst = S + lane * p32;
+        if (off == 0) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int r = lane + 32 * q;
-        if (r < M) {
-            float *dst = S + r * p32;
-            if (off == 0) {
-                float4 *d4 = reinterpret_cast<float4 *>(dst);
+            for (int c4 = 0; c4 < WC4; ++c4)
+                d4[c4] = make_float4(A0[2 * c4].x, A0[2 * c4].y, A0[2 * c4 + 1].x, A0[2 * c4 + 1].y);
+        } else {
 #pragma unroll
-                for (int c4 = 0; c4 < WC4; ++c4)
-                    d4[c4] = make_float4(Rw[q][2 * c4].x, Rw[q][2 * c4].y, Rw[q][2 * c4 + 1].x,
-                                         Rw[q][2 * c4 + 1].y);
-            } else {
-#pragma unroll
-                for (int j = 0; j < W2; ++j) {
-                    if (2 * j >= off) dst[2 * j - off] = Rw[q][j].x;
-                    if (2 * j + 1 >= off) dst[2 * j + 1 - off] = Rw[q][j].y;
-                }
+            for (int j = 0; j < W2; ++j) {
+                if (2 * j >= off) dst[2 * j - off] = A0[j].x;
+                if (2 * j + 1 >= off) dst[2 * j + 1 - off] = A0[j].y;
             }
         }
     }
+    if (r1 < M) {
+        float *dst = S + r1 * p32;
+#pragma unroll
+        for (int j = 0; j < PC2; ++j) {
+            const int c = c1base + 2 * j - off;
+            if (c >= 0) dst[c] = A1[j].x;
+            if (c + 1 >= 0) dst[c + 1] = A1[j].y;
+        }
+    }
+    // pivot steps in the row-per-lane layout of the apply (row 32 + lane)
+    step[0] = st0;
+    const int s1 = __shfl_sync(kFull, st1, (lane * PARTS) & 31);
+    if (lane < W - 32) step[1] = s1;
     __syncwarp();
     return ok;
 }
@@ -1341,7 +1360,7 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
     n1 = warp_maxf(n1);
     bool queue;
     if constexpr (W > 0)
-        queue = !gj32_invert_reg<RPL, W>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
+        queue = !gj32_invert_reg<W>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
     else
         queue = !gj32_invert<RPL>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
     if (!queue) {
