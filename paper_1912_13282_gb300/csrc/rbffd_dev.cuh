@@ -976,21 +976,28 @@ __device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int 
     const int lane = threadIdx.x & 31;
     const int l = P.l, k = P.k, di = DIM - 2;
     float amax = 0.0f;
-    for (int d = 1; d <= n / 2; ++d) {
-        const int cnt = (2 * d == n) ? n / 2 : n;
-        for (int r = lane; r < cnt; r += 32) {
-            int c = r + d;
-            if (c >= n) c -= n;
-            float2 r2 = make_float2(0.0f, 0.0f);
+    // the n (n - 1) / 2 unordered pairs (r, (r + d) mod n), d = 1 .. n/2 (r < n/2
+    // for d = n/2), numbered t = (d - 1) n + r and dealt to the lanes in turn
+    const int npairs = n * (n - 1) / 2;
+    int d = 1 + lane / max(n, 1), r = lane % max(n, 1);
+#pragma unroll 2
+    for (int t = lane; t < npairs; t += 32) {
+        int c = r + d;
+        if (c >= n) c -= n;
+        float2 r2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                const float2 t = ff_sub(xf[r * DIM + a], xf[c * DIM + a]);
-                r2 = ff_add(r2, ff_mul(t, t));
-            }
-            const float2 v = ff_phs(r2, k);
-            A[r * pA + c] = v;
-            A[c * pA + r] = v;
-            amax = fmaxf(amax, v.x);
+        for (int a = 0; a < DIM; ++a) {
+            const float2 dx = ff_sub(xf[r * DIM + a], xf[c * DIM + a]);
+            r2 = ff_add(r2, ff_mul(dx, dx));
+        }
+        const float2 v = ff_phs(r2, k);
+        A[r * pA + c] = v;
+        A[c * pA + r] = v;
+        amax = fmaxf(amax, v.x);
+        r += 32;
+        while (r >= n) {
+            r -= n;
+            ++d;
         }
     }
     for (int r = lane; r < n; r += 32) {
@@ -1167,18 +1174,19 @@ struct WideFF {
         return ff_fast_sum(t.x, __fadd_rn(t.y, x.y));
     }
     static __device__ __forceinline__ double to_d(T x) { return (double)x.x + (double)x.y; }
+    // rows i < n: A row i then Q row i; rows n + b: column b of Q.  One loop
+    // serves both kinds (base and stride per lane), so lanes of a warp on
+    // different kinds do not run both loops.
     static __device__ __forceinline__ float residual(const T *A, int pA, const T *Q, int l, const T *B,
                                                      const T *X, int n, int R, int i, int c) {
         FFAcc acc(B[i * R + c]);
-        if (i < n) {
-            const T *Ai = A + i * pA;
-            const T *Qi = Q + i * l;
-            for (int j = 0; j < n; ++j) acc.sub(Ai[j], X[j * R + c]);
-            for (int b = 0; b < l; ++b) acc.sub(Qi[b], X[(n + b) * R + c]);
-        } else {
-            const int b = i - n;
-            for (int j = 0; j < n; ++j) acc.sub(Q[j * l + b], X[j * R + c]);
-        }
+        const bool arow = i < n;
+        const T *p1 = arow ? A + i * pA : Q + (i - n);
+        const int s1 = arow ? 1 : l;
+        for (int j = 0; j < n; ++j) acc.sub(p1[j * s1], X[j * R + c]);
+        const T *p2 = arow ? Q + i * l : Q;
+        const int n2 = arow ? l : 0;
+        for (int b = 0; b < n2; ++b) acc.sub(p2[b], X[(n + b) * R + c]);
         return acc.value();
     }
 };
