@@ -543,12 +543,12 @@ def run_disk(args, rk):
     f32 = mixed_fp32_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
     dom_ms = float(np.mean(dom))
     achieved = f32 / (dom_ms * 1e-3)
-    traffic = stored_traffic("k_weights_mixed<2,2,3>")
+    traffic = stored_traffic("k_weights_mixed<2,2,3,40>")
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak,
             "traffic": None if traffic is None else traffic["bytes_per_row"] * Ni,
-            "kernel": "k_weights_mixed<2,2,3> (interior rows; FP32 Gauss-Jordan inverse + "
-                      "double-FP32 refinement)",
+            "kernel": "k_weights_mixed<2,2,3,40> (interior rows; FP32 Gauss-Jordan inverse with the "
+                      "rows in registers + double-FP32 refinement)",
             "algorithmic": "FP32 flops per interior stencil: inverse 2M^3, products with it, "
                            "compensated residuals, double-FP32 assembly (bench.mixed_fp32_flops)",
             "peak_source": "FP32 FMA peak measured in this run (mm_measure_fma_peak); "
