@@ -625,10 +625,18 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
         }
     };
     auto lead_of = [](int p) { return p < 32 ? p : (p - 32) * PARTS; };
-    bool ok = true;
-    int kk = 0;
-    for (; kk + 1 < M; kk += 2) {
-        // first pivot: column kk (register 0)
+    // The two pivots of the pass that eliminates the frame's columns 0 and 1
+    // (the pivot rows' steps are recorded when that pass runs).  Each pass
+    // chooses the next pass's pivots as soon as its own update has produced
+    // the new columns 0 and 1, so the choice overlaps the rest of the update.
+    struct Piv {
+        int p1, p2;
+        float ip1, ip2, u1n, m1p2, u2k, m10, c10, m11, c11;
+        bool good;
+    };
+    auto choose = [&]() {
+        Piv v;
+        // first pivot: column 0
         unsigned key = 0;
         if (st0 == kBig) key = pivot_key(A0[0].x, lane);
         if (pt == 0 && st1 == kBig) key = max(key, pivot_key(A1[0].x, r1));
@@ -639,26 +647,46 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
         const float p1c1 = __shfl_sync(kFull, h1.y, lead_of(p1));
         const bool good1 = fabsf(piv1) > tiny;
         const float ip1 = good1 ? __frcp_rn(piv1) : 0.0f;
-        const float u1n = p1c1 * ip1;              // u1 at column kk+1
-        // multiplier of step 1 and column kk+1 after step 1 (row r1's from its lead lane)
+        const float u1n = p1c1 * ip1;              // u1 at column 1
+        // multiplier of step 1 and column 1 after step 1 (row r1's from its lead lane)
         const float m10 = A0[0].x, c10 = fmaf(-m10, u1n, A0[0].y);
         float m11 = A1[0].x, c11 = fmaf(-m11, u1n, A1[0].y);
         m11 = __shfl_sync(kFull, m11, lead);
         c11 = __shfl_sync(kFull, c11, lead);
+        // second pivot: column 1 after step 1, among the rows other than p1
         unsigned key2 = 0;
-        if (lane == p1) st0 = kk;
-        else if (lane < M && st0 == kBig) key2 = pivot_key(c10, lane);
-        if (r1 == p1) st1 = kk;
-        else if (pt == 0 && r1 < M && st1 == kBig) key2 = max(key2, pivot_key(c11, r1));
-        // second pivot: column kk+1 after step 1
+        if (lane != p1 && lane < M && st0 == kBig) key2 = pivot_key(c10, lane);
+        if (r1 != p1 && pt == 0 && r1 < M && st1 == kBig) key2 = max(key2, pivot_key(c11, r1));
         int p2 = pivot_row(key2);
         if (p2 == kBig) p2 = p1 == 0 ? 1 : 0;      // not reached
         const float m1p2 = __shfl_sync(kFull, p2 < 32 ? m10 : m11, lead_of(p2));
         const float piv2 = __shfl_sync(kFull, p2 < 32 ? c10 : c11, lead_of(p2));
         const bool good2 = fabsf(piv2) > tiny;
-        ok &= good1 && good2;
         const float ip2 = good2 ? __frcp_rn(piv2) : 0.0f;
-        const float u2k = -m1p2 * ip1 * ip2;       // u2 at column kk
+        v.p1 = p1;
+        v.p2 = p2;
+        v.ip1 = ip1;
+        v.ip2 = ip2;
+        v.u1n = u1n;
+        v.m1p2 = m1p2;
+        v.u2k = -m1p2 * ip1 * ip2;                 // u2 at column 0
+        v.m10 = m10;
+        v.c10 = c10;
+        v.m11 = m11;
+        v.c11 = c11;
+        v.good = good1 && good2;
+        return v;
+    };
+    bool ok = true;
+    int kk = 0;
+    Piv pv = choose();
+    for (; kk + 1 < M; kk += 2) {
+        const int p1 = pv.p1, p2 = pv.p2;
+        const float ip1 = pv.ip1, ip2 = pv.ip2, u1n = pv.u1n, m1p2 = pv.m1p2, u2k = pv.u2k;
+        const float m10 = pv.m10, c10 = pv.c10, m11 = pv.m11, c11 = pv.c11;
+        ok &= pv.good;
+        if (lane == p1) st0 = kk;
+        if (r1 == p1) st1 = kk;
         if (lane == p2) st0 = kk + 1;
         if (r1 == p2) st1 = kk + 1;
         put_row(p1, P1);
@@ -706,8 +734,9 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
         __syncwarp();
         const float4 *U4 = reinterpret_cast<const float4 *>(U);
         const float4 *V4 = reinterpret_cast<const float4 *>(V);
-#pragma unroll
-        for (int c4 = 0; c4 < WC4; ++c4) {
+        const float2 *U2 = reinterpret_cast<const float2 *>(U + c1base);
+        const float2 *V2 = reinterpret_cast<const float2 *>(V + c1base);
+        auto update0 = [&](int c4) {
             const float4 u = U4[c4], v = V4[c4];
             const float2 o0 = A0[2 * c4 + 1];
             const float2 o1v = 2 * c4 + 2 < W2 ? A0[2 * c4 + 2] : zero2;
@@ -717,15 +746,20 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
             hi = ffma2(b10, make_float2(u.z, u.w), hi);
             A0[2 * c4] = ffma2(b20, make_float2(v.x, v.y), lo);
             A0[2 * c4 + 1] = ffma2(b20, make_float2(v.z, v.w), hi);
-        }
-        const float2 *U2 = reinterpret_cast<const float2 *>(U + c1base);
-        const float2 *V2 = reinterpret_cast<const float2 *>(V + c1base);
-#pragma unroll
-        for (int j = 0; j < PC2; ++j) {
+        };
+        auto update1 = [&](int j) {
             const float2 o = j + 1 < PC2 ? A1[j + 1] : nxt;
             const float2 t = ffma2(b11, U2[j], ffma2(al1, o, zero2));
             A1[j] = ffma2(b21, V2[j], t);
-        }
+        };
+        // the next frame's columns 0 and 1, then the next pass's pivots, then the rest
+        update0(0);
+        update1(0);
+        pv = choose();
+#pragma unroll
+        for (int c4 = 1; c4 < WC4; ++c4) update0(c4);
+#pragma unroll
+        for (int j = 1; j < PC2; ++j) update1(j);
     }
     if (kk < M) {
         // last column of an odd-sized system: one rank-1 step, shift by one
