@@ -577,7 +577,7 @@ __device__ __forceinline__ bool gj32_invert(float *__restrict__ S, int p32, int 
 // give identical inverses.
 template <int W>
 __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, int M, int *step, int *perm,
-                                                float *__restrict__ buf, float tiny) {
+                                                float *__restrict__ buf, float tiny, float &nK, float &nKinv) {
     static_assert(W == 40 || W == 48, "register width");
     constexpr int W2 = W / 2, WC4 = W / 4;
     constexpr int PARTS = 32 / (W - 32), PC = W / PARTS, PC2 = PC / 2;
@@ -625,6 +625,34 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
         }
     };
     auto lead_of = [](int p) { return p < 32 ? p : (p - 32) * PARTS; };
+    // max over rows of the row sums of |entries| of the frame (columns past
+    // the matrix hold zeros); row r1's pieces are added in column order, lane
+    // to lane, so every sum is formed in the order of the shared-memory form
+    auto rows_norm = [&]() {
+        float rs0 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < W2; ++j) {
+            rs0 += fabsf(A0[j].x);
+            rs0 += fabsf(A0[j].y);
+        }
+        float rs1 = 0.0f;
+#pragma unroll
+        for (int t = 0; t < PARTS; ++t) {
+            const float in = __shfl_up_sync(kFull, rs1, 1);
+            if (pt == t) {
+                rs1 = t == 0 ? 0.0f : in;
+#pragma unroll
+                for (int j = 0; j < PC2; ++j) {
+                    rs1 += fabsf(A1[j].x);
+                    rs1 += fabsf(A1[j].y);
+                }
+            }
+        }
+        float v = lane < M ? rs0 : 0.0f;
+        if (last && r1 < M) v = fmaxf(v, rs1);
+        return warp_maxf(v);
+    };
+    nK = rows_norm();
     // The two pivots of the pass that eliminates the frame's columns 0 and 1
     // (the pivot rows' steps are recorded when that pass runs).  Each pass
     // chooses the next pass's pivots as soon as its own update has produced
@@ -809,6 +837,7 @@ __device__ __forceinline__ bool gj32_invert_reg(float *__restrict__ S, int p32, 
             A1[j] = ffma2(bb1, U2[j], ffma2(al1, o, zero2));
         }
     }
+    nKinv = rows_norm();
     // the inverse: columns W - M .. W - 1 of the registers -> columns 0 .. M-1 of S
     const int off = W - M;
     if (lane < M) {
@@ -1003,10 +1032,12 @@ __device__ inline float2 ff_phs_d2(int op, int k, float2 r2, float2 rk2, const f
 
 // The system for the residuals in double-FP32: A [n x pA] (diagonal 0), Q
 // [n x l], B [M x R] (rows < n: l_phi, rows n + b: l_q), from the scaled
-// offsets xf [n x DIM] (double-FP32).  Returns max |K| over A and Q (FP32).
+// offsets xf [n x DIM] (double-FP32).  The leading FP32 parts of A, Q and Q^T
+// go to the FP32 system S [rows x p32] as they are formed (its zero block and
+// padding are the caller's).  Returns max |K| over A and Q (FP32).
 template <int DIM>
 __device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int n, const float2 *xf, float2 *A, int pA,
-                             float2 *Q, float2 *B, int R) {
+                             float2 *Q, float2 *B, int R, float *S, int p32) {
     const int lane = threadIdx.x & 31;
     const int l = P.l, k = P.k, di = DIM - 2;
     float amax = 0.0f;
@@ -1027,6 +1058,8 @@ __device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int 
         const float2 v = ff_phs(r2, k);
         A[r * pA + c] = v;
         A[c * pA + r] = v;
+        S[r * p32 + c] = v.x;
+        S[c * p32 + r] = v.x;
         amax = fmaxf(amax, v.x);
         r += 32;
         while (r >= n) {
@@ -1036,11 +1069,16 @@ __device__ __forceinline__ float assemble_ff(const WParams &P, int64_t row, int 
     }
     for (int r = lane; r < n; r += 32) {
         A[r * pA + r] = make_float2(0.0f, 0.0f);
+        S[r * p32 + r] = 0.0f;
         float2 *Qr = Q + r * l;
         Qr[0] = make_float2(1.0f, 0.0f);
+        S[r * p32 + n] = 1.0f;
+        S[n * p32 + r] = 1.0f;
         for (int b = 1; b < l; ++b) {
             const float2 v = ff_mul(Qr[c_mono.parent[di][b]], xf[r * DIM + c_mono.var[di][b]]);
             Qr[b] = v;
+            S[r * p32 + n + b] = v.x;
+            S[(n + b) * p32 + r] = v.x;
             amax = fmaxf(amax, fabsf(v.x));
         }
         float2 r2 = make_float2(0.0f, 0.0f);
@@ -1355,7 +1393,7 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
         for (int j = lane; j < n * DIM; j += 32) xf[j] = ff_from_double(xi[j]);
         __syncwarp();
         amax = assemble_ff<DIM>(P, row, n, xf, (float2 *)(base + Ly.a64), pA, (float2 *)(base + Ly.q64),
-                                (float2 *)(base + Ly.b64), R);
+                                (float2 *)(base + Ly.b64), R, S, p32);
     }
     // FP32 system: the leading parts (own rows; Q^T entries written by the row's owner)
     int step[RPL];
@@ -1366,18 +1404,12 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
         const int r = lane + 32 * q;
         step[q] = r < M ? kBig : -1;
         if (r < n) {
-            float *Sr = S + r * p32;
+            // (the double-FP32 assembly wrote its leading parts as it went)
             if (P.wide64) {
+                float *Sr = S + r * p32;
                 for (int c = 0; c < n; ++c) Sr[c] = (float)A64[r * pA + c];
                 for (int b = 0; b < l; ++b) {
                     const float v = (float)Q64[r * l + b];
-                    Sr[n + b] = v;
-                    S[(n + b) * p32 + r] = v;
-                }
-            } else {
-                for (int c = 0; c < n; ++c) Sr[c] = Af[r * pA + c].x;
-                for (int b = 0; b < l; ++b) {
-                    const float v = Qf[r * l + b].x;
                     Sr[n + b] = v;
                     S[(n + b) * p32 + r] = v;
                 }
@@ -1389,36 +1421,30 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
             for (int c = M; c < W4; ++c) S[r * p32 + c] = 0.0f;
     }
     __syncwarp();
-    float n1 = 0.0f;   // ||K||_1 = max row sum (symmetric)
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const int r = lane + 32 * q;
-        if (r < M) {
-            float rs = 0.0f;
-            for (int c = 0; c < M; ++c) rs += fabsf(S[r * p32 + c]);
-            n1 = fmaxf(n1, rs);
-        }
-    }
-    n1 = warp_maxf(n1);
+    // ||K||_1 and ||K^-1||_1 as max row sums (K and its inverse are symmetric)
+    float n1 = 0.0f, ninv = 0.0f;
     bool queue;
-    if constexpr (W > 0)
-        queue = !gj32_invert_reg<W>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
-    else
-        queue = !gj32_invert<RPL>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
-    if (!queue) {
-        float ninv = 0.0f;
+    if constexpr (W > 0) {
+        queue = !gj32_invert_reg<W>(S, p32, M, step, perm, U32, (float)M * u32 * amax, n1, ninv);
+    } else {
+        auto rows_norm = [&]() {
+            float v = 0.0f;
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-            const int r = lane + 32 * q;
-            if (r < M) {
-                float rs = 0.0f;
-                for (int c = 0; c < M; ++c) rs += fabsf(S[r * p32 + c]);
-                ninv = fmaxf(ninv, rs);
+            for (int q = 0; q < RPL; ++q) {
+                const int r = lane + 32 * q;
+                if (r < M) {
+                    float rs = 0.0f;
+                    for (int c = 0; c < M; ++c) rs += fabsf(S[r * p32 + c]);
+                    v = fmaxf(v, rs);
+                }
             }
-        }
-        ninv = warp_maxf(ninv);
-        queue = !((double)n1 * (double)ninv * u32 <= P.kappa_max);
+            return warp_maxf(v);
+        };
+        n1 = rows_norm();
+        queue = !gj32_invert<RPL>(S, p32, M, step, perm, U32, (float)M * u32 * amax);
+        if (!queue) ninv = rows_norm();
     }
+    if (!queue) queue = !((double)n1 * (double)ninv * u32 <= P.kappa_max);
     bool conv = false;
     if (!queue) {
         if (P.wide64)
