@@ -65,7 +65,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="disk", choices=["disk", "ball", "batch", "surrogate"])
+    ap.add_argument("--workload", default="disk", choices=["disk", "ball", "batch", "surrogate", "wls"])
     ap.add_argument("--n-target", type=int, default=None, help="override the node count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -697,6 +697,139 @@ def run_ball(args, rk):
     return line
 
 
+# ----------------------------------------------------------- GWLS workload
+WLS = {"workload": "GWLS weights (Section 2.2.1) on the disk minus 5 holes, 1e6 nodes: interior rows, "
+                   "9 closest nodes, monomials of degree <= 2, Gaussian weight sigma = 1, closest-node "
+                   "scale (the paper's GWLS example setup); lap, dx, dy",
+       "N_target": 1_000_000, "n": 9, "m": 2, "sigma": 1.0, "ops": 1 | 2 | 4}
+
+
+def wls_fp64_flops(n, l, R):
+    """Algorithmic FP64 flops of one GWLS stencil: Householder QR of the n x l
+    matrix W B (2 n l^2 - 2 l^3 / 3), R forward substitutions (l^2 each),
+    R products with Q (4 n l - 2 l^2 each) and W B itself (n l)."""
+    return 2 * n * l * l - 2 * l ** 3 / 3 + R * l * l + R * (4 * n * l - 2 * l * l) + n * l
+
+
+def cpu_baseline_wls(ns, col_h, rp_h, rows, seconds=10.0):
+    """oracle/wls.py (numpy, one stencil at a time) on a bounded sample."""
+    from oracle import wls as Wo
+    import time as _t
+    t0 = _t.perf_counter()
+    done = 0
+    for i in rows:
+        x = ns.pts[col_h[rp_h[i]:rp_h[i + 1]]]
+        Wo.stencil_weights(x, WLS["m"], WLS["ops"], WLS["sigma"], Wo.SCALE_NEAREST)
+        done += 1
+        if _t.perf_counter() - t0 > seconds:
+            break
+    dt = _t.perf_counter() - t0
+    return {"value": done / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} interior stencils of the same node set (numpy SVD pseudoinverse, one thread)"}
+
+
+def run_wls(args, rk):
+    import torch
+
+    import nodesets as NS
+    import paper_1912_13282_gb300 as P
+    device = rk.local
+    stream = torch.cuda.current_stream(device)
+    ctx = P.Context(device, stream)
+    ns = NS.disk_holes(args.n_target or WLS["N_target"], seed=rk.rank)
+    b, e = ns.classes["interior"]
+    n, m, R = WLS["n"], WLS["m"], 3
+    rp = np.zeros(ns.N + 1, dtype=np.int64)
+    rp[b + 1:e + 1] = np.arange(1, e - b + 1) * n
+    rp[e + 1:] = rp[e]
+    dv = f"cuda:{device}"
+    pts = torch.from_numpy(ns.pts).to(dv)
+    rp_d = torch.from_numpy(rp).to(dv)
+    nnz = int(rp[-1])
+    col = torch.empty(nnz, dtype=torch.int32, device=dv)
+    vals = [torch.zeros(nnz, dtype=torch.float64, device=dv) for _ in range(R)]
+    status = torch.empty(ns.N, dtype=torch.int32, device=dv)
+    ranges = [(b, e, n, col)]
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dv)
+    fp64_peak = ctx.measure_fma_peak(0)
+
+    def weights():
+        ctx.wls_weights(WLS["ops"], m, WLS["sigma"], P.SCALE_NEAREST, pts, rp_d, col, vals, row_begin=b,
+                        row_end=e, n_max=n, status=status)
+
+    for _ in range(max(3, args.warmup)):
+        ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
+        weights()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    rk.barrier()
+    tt, ww = [], []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
+        ev[1].record(stream)
+        weights()
+        ev[2].record(stream)
+        ev[2].synchronize()
+        tt.append(ev[0].elapsed_time(ev[2]))
+        ww.append(ev[1].elapsed_time(ev[2]))
+    clk = clocks.stop()
+    (ms,) = rk.max([float(np.sum(tt))])
+    (msw,) = rk.max([float(np.sum(ww))])
+    Ni = e - b
+    (n_all,) = rk.sum([Ni])
+    # end to end through the public calls: host points in, weights out (pinned)
+    e2e = None
+    if not args.no_e2e:
+        h_pts = torch.from_numpy(ns.pts).pin_memory()
+        h_out = [torch.empty(nnz, dtype=torch.float64).pin_memory() for _ in range(R)]
+        e_ms = []
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pts.copy_(h_pts, non_blocking=True)
+            ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
+            weights()
+            for h, d in zip(h_out, vals):
+                h.copy_(d, non_blocking=True)
+            z.record(stream)
+            z.synchronize()
+            e_ms.append(a.elapsed_time(z))
+        (e_tot,) = rk.max([float(np.sum(e_ms))])
+        e2e = {"value": throughput(n_all, e_tot, args.steps), "unit": "nodes/s",
+               "h2d_bytes_per_step": int(h_pts.numel() * 8), "d2h_bytes_per_step": int(nnz * 8 * R)}
+    st = status.cpu().numpy()[b:e]
+    l = 6
+    flops = wls_fp64_flops(n, l, R) * Ni
+    w_ms = msw / args.steps
+    roof = {"bound": "alu", "kernel": "k_wls_thread<2> (FP64 Householder QR, one stencil per thread)",
+            "achieved": flops / (w_ms * 1e-3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": flops / (w_ms * 1e-3) / fp64_peak, "traffic": None,
+            "algorithmic": "bench.wls_fp64_flops: %.0f FP64 flops per stencil" % wls_fp64_flops(n, l, R),
+            "peak_source": "FP64 FMA peak measured in this run (mm_measure_fma_peak)"}
+    line = {"metric": "GWLS stencil weights nodes/s", "value": throughput(n_all, msw, args.steps),
+            "unit": "nodes/s", "n_gpus": rk.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": w_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WLS["workload"], "N": ns.N, "rows": Ni,
+                       "l2": "256 MiB buffer written between timed steps"},
+            "with_knn": {"value": throughput(n_all, ms, args.steps), "unit": "nodes/s",
+                         "ms_per_step": ms / args.steps},
+            "status_ok_fraction": float((st == 0).mean()), "roofline": roof, "e2e": e2e,
+            "clocks": clk, "gpu_launches": 6 * args.steps}
+    if rk.rank == 0 and rk.world == 1 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(0)
+        sample = rng.choice(np.arange(b, e), 4000, replace=False)
+        # the rows before b are empty, so col is indexed by the full row pointer
+        line["cpu_baseline"] = cpu_baseline_wls(ns, col.cpu().numpy(), rp, sample)
+    ctx.close()
+    return line
+
+
 # ----------------------------------------------------------- batch workload
 def run_batch(args, rk):
     import torch
@@ -919,7 +1052,8 @@ def main(argv=None):
     if rk.local == 0:
         _build.build()
     rk.barrier()
-    run = {"disk": run_disk, "ball": run_ball, "batch": run_batch, "surrogate": run_surrogate}[args.workload]
+    run = {"disk": run_disk, "ball": run_ball, "batch": run_batch, "surrogate": run_surrogate,
+           "wls": run_wls}[args.workload]
     line = run(args, rk)
     if rk.rank == 0:
         print(json.dumps(line), flush=True)

@@ -191,6 +191,35 @@ int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N
                      const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
                      int n_max, int precision, double *const *d_vals, int32_t *d_status);
 
+/* ------------------------------------------------------- GWLS weights */
+#define MM_SCALE_FARTHEST 0   /* s = largest distance from the centre in the stencil */
+#define MM_SCALE_NEAREST 1    /* s = distance to the closest other node            */
+
+/*
+ * Generalized weighted least squares weights (Section 2.2.1): for every row i
+ * in [row_begin, row_end), with x_c the centre, xi_j = (x_j - x_c)/s, the
+ * monomials b of total degree <= m (graded order), B_jb = b(xi_j) and
+ * W = diag(omega(xi_j)), omega(x) = exp(-|x|^2 / sigma^2), the weights are
+ *     w^T = (L b)(0)^T (W B)^+ W,
+ * i.e. w = W y with y the minimum-norm solution of (W B)^T y = (L b)(0);
+ * stored as w / s^q like mm_rbffd_weights.  Computed in FP64 by a Householder
+ * QR of W B (one warp per stencil).
+ *   ops, m, dim, N, d_pts, d_normals, stencils, row range, d_vals, d_status:
+ *              as mm_rbffd_weights (no k; n_max <= 64).
+ *   sigma      Gaussian width, finite and > 0 (in scaled units).
+ *   scale      MM_SCALE_FARTHEST or MM_SCALE_NEAREST (the paper's example
+ *              setup scales to the closest node).
+ * Rows with fewer nodes than monomials, or with W B of numerically deficient
+ * rank, get MM_ST_SINGULAR and zero weights; bad rows (index out of range,
+ * centre not first, n_i outside [1, n_max], a single node with
+ * MM_SCALE_NEAREST) get MM_ST_BADARG and zero weights.
+ * Errors: MM_EBADARG, MM_EUNSUPPORTED (n_max > 64), MM_ECUDA.
+ */
+int mm_wls_weights(mm_ctx *ctx, unsigned ops, int m, double sigma, int scale, int dim, int64_t N,
+                   const double *d_pts, const double *d_normals, const mm_csr_pattern *stencils,
+                   int64_t row_begin, int64_t row_end, int n_max, double *const *d_vals,
+                   int32_t *d_status);
+
 /* ----------------------------------------------- batched (mixed) classes */
 /*
  * One stencil class for mm_rbffd_weights_batched: the arguments of one

@@ -25,6 +25,7 @@ OPT_IR_TOL, OPT_IR_MAX_STEPS, OPT_KAPPA_MAX, OPT_WIDE, OPT_MLP_INFER, OPT_GJ = 1
 WIDE_FF, WIDE_FP64 = 0, 1
 MLP_FUSED, MLP_LAYERED = 0, 1
 GJ_AUTO, GJ_SHARED = 0, 1
+SCALE_FARTHEST, SCALE_NEAREST = 0, 1
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
@@ -33,7 +34,7 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_tile_table_load", "mm_mlp_create", "mm_mlp_destroy", "mm_mlp_num_params",
            "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_output_scaling",
            "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
-           "mm_stencil_features", "mm_rbffd_weights_surrogate"]
+           "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights"]
 
 
 class KnnRange(C.Structure):
@@ -97,6 +98,8 @@ def load():
                                                     C.c_int, C.POINTER(vp), vp]
         lib.mm_rbffd_weights_batched.argtypes = [vp, C.c_int, C.POINTER(WeightsClass), C.c_int,
                                                  C.POINTER(LaunchConfig)]
+        lib.mm_wls_weights.argtypes = [vp, C.c_uint, C.c_int, dbl, C.c_int, C.c_int, i64, vp, vp,
+                                       C.POINTER(CsrPattern), i64, i64, C.c_int, C.POINTER(vp), vp]
         lib.mm_autotune_batched.argtypes = [vp, C.c_int, C.POINTER(WeightsClass), C.c_int, i64,
                                             C.POINTER(LaunchConfig), C.POINTER(dbl)]
         lib.mm_tile_table_save.argtypes = [vp, C.c_char_p]
@@ -229,6 +232,35 @@ class Context:
         self._check(self._lib.mm_rbffd_weights(self._h, ops, k, m, dim, N, _ptr(pts),
                                                _ptr(normals), C.byref(pat), row_begin, row_end,
                                                n_max, precision, vp, _ptr(status)))
+
+    def wls_weights(self, ops: int, m: int, sigma: float, scale: int, pts: torch.Tensor,
+                    row_ptr: torch.Tensor, col: torch.Tensor, vals, row_begin: int = 0,
+                    row_end: int | None = None, n_max: int | None = None,
+                    normals: torch.Tensor | None = None, status: torch.Tensor | None = None):
+        """GWLS weights (mm_wls_weights); vals as for rbffd_weights."""
+        _dev(pts, "pts", torch.float64)
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        N, dim = pts.shape
+        nrows = row_ptr.numel() - 1
+        if row_end is None:
+            row_end = nrows
+        if n_max is None:
+            raise MMError("n_max (largest stencil size in the row range) is required")
+        nbits = bin(ops).count("1")
+        if len(vals) != nbits:
+            raise MMError(f"{nbits} value arrays expected")
+        for v in vals:
+            _dev(v, "vals", torch.float64)
+        if normals is not None:
+            _dev(normals, "normals", torch.float64)
+        if status is not None:
+            _dev(status, "status", torch.int32)
+        pat = CsrPattern(nrows, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        vp = (C.c_void_p * max(1, nbits))(*[v.data_ptr() for v in vals])
+        self._check(self._lib.mm_wls_weights(self._h, ops, m, float(sigma), scale, dim, N, _ptr(pts),
+                                             _ptr(normals), C.byref(pat), row_begin, row_end, n_max,
+                                             vp, _ptr(status)))
 
     def rbffd_weights_ir_noalloc(self, ops: int, k: int, m: int, pts, row_ptr, col, vals,
                                  row_begin: int = 0, row_end: int | None = None,

@@ -1,6 +1,7 @@
 // The C ABI (mm.h): argument validation on the host, context and workspace
 // management, dispatch to the kernels.  No exception leaves this file.
 #include <stdarg.h>
+#include <math.h>
 #include <stdio.h>
 
 #include <map>
@@ -13,6 +14,7 @@
 int rbffd_init_device(mm_ctx *ctx);
 int batched_init_device(mm_ctx *ctx);
 int mlp_init_device(mm_ctx *ctx);
+int wls_init_device(mm_ctx *ctx);
 
 int mm_fail(mm_ctx *ctx, int code, const char *fmt, ...) {
     if (ctx) {
@@ -101,7 +103,8 @@ bool bad_dim(int dim) { return dim != 2 && dim != 3; }
 int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
                           const double *d_pts, const double *d_normals,
                           const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
-                          int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job) {
+                          int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job,
+                          bool wls) {
     if (bad_dim(dim)) return mm_fail(ctx, MM_EBADARG, "dim must be 2 or 3");
     if (ops == 0 || ops >= 2048u) return mm_fail(ctx, MM_EBADARG, "ops must be a nonzero MM_* bitmask");
     if ((ops & (MM_DZ | MM_DXZ | MM_DYZ | MM_DZZ)) && dim != 3)
@@ -109,7 +112,7 @@ int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int6
     if ((ops & (MM_DXX | MM_DXY | MM_DYY | MM_DXZ | MM_DYZ | MM_DZZ)) && m < 2)
         return mm_fail(ctx, MM_EBADARG, "second derivatives need monomials of degree >= 2");
     if ((ops & MM_DN) && !d_normals) return mm_fail(ctx, MM_EBADARG, "MM_DN needs d_normals");
-    if (k != 3 && k != 5 && k != 7) return mm_fail(ctx, MM_EBADARG, "k must be 3, 5 or 7");
+    if (!wls && k != 3 && k != 5 && k != 7) return mm_fail(ctx, MM_EBADARG, "k must be 3, 5 or 7");
     if (m < 0 || m > 6) return mm_fail(ctx, MM_EBADARG, "m must be in [0, 6]");
     if (N < 1 || N >= (int64_t(1) << 31) || !d_pts) return mm_fail(ctx, MM_EBADARG, "bad points");
     if (!stencils || !stencils->d_row_ptr || !stencils->d_col)
@@ -141,8 +144,11 @@ int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int6
             J.vals[b] = d_vals[r++];
         }
     }
-    if (n_max + mm_num_monomials(dim, m) > 96)
+    if (wls) {
+        if (n_max > 64) return mm_fail(ctx, MM_EUNSUPPORTED, "n_max = %d > 64", n_max);
+    } else if (n_max + mm_num_monomials(dim, m) > 96) {
         return mm_fail(ctx, MM_EUNSUPPORTED, "n_max + l = %d > 96", n_max + mm_num_monomials(dim, m));
+    }
     return MM_OK;
 }
 
@@ -175,7 +181,7 @@ int mm_ctx_create(mm_ctx **out, int device, void *cuda_stream) {
     ctx->smem_optin = (size_t)optin;
     if (rbffd_init_device(ctx) != MM_OK || batched_init_device(ctx) != MM_OK ||
         mlp_init_device(ctx) != MM_OK || mixed_init_device_2d(ctx) != MM_OK ||
-        mixed_init_device_3d(ctx) != MM_OK) {
+        mixed_init_device_3d(ctx) != MM_OK || wls_init_device(ctx) != MM_OK) {
         delete ctx;
         return MM_ECUDA;
     }
@@ -269,6 +275,23 @@ int mm_rbffd_weights(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N
     if (rc != MM_OK) return rc;
     DeviceGuard g(ctx);
     return weights_launch(ctx, job, precision);
+}
+
+int mm_wls_weights(mm_ctx *ctx, unsigned ops, int m, double sigma, int scale, int dim, int64_t N,
+                   const double *d_pts, const double *d_normals, const mm_csr_pattern *stencils,
+                   int64_t row_begin, int64_t row_end, int n_max, double *const *d_vals,
+                   int32_t *d_status) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (!(sigma > 0.0) || !isfinite(sigma)) return mm_fail(ctx, MM_EBADARG, "sigma must be finite and > 0");
+    if (scale != MM_SCALE_FARTHEST && scale != MM_SCALE_NEAREST)
+        return mm_fail(ctx, MM_EBADARG, "scale must be MM_SCALE_FARTHEST or MM_SCALE_NEAREST");
+    WeightsJob job{};
+    int rc = weights_job_from_args(ctx, ops, 3, m, dim, N, d_pts, d_normals, stencils, row_begin,
+                                   row_end, n_max, d_vals, d_status, &job, true);
+    if (rc != MM_OK) return rc;
+    DeviceGuard g(ctx);
+    return wls_launch(ctx, job, sigma, scale);
 }
 
 int mm_apply_operator(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,

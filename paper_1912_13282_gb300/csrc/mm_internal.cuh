@@ -111,6 +111,8 @@ int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision);
 // FP32 + refinement kernel of one class (2D / 3D); handed-over rows go to fb_list
 int mixed_launch_2d(mm_ctx *ctx, const WeightsJob &job, int *fb_count, int *fb_list);
 int mixed_launch_3d(mm_ctx *ctx, const WeightsJob &job, int *fb_count, int *fb_list);
+// GWLS weights (wls.cu) of a validated job (k unused)
+int wls_launch(mm_ctx *ctx, const WeightsJob &job, double sigma, int scale);
 int mixed_init_device_2d(mm_ctx *ctx);
 int mixed_init_device_3d(mm_ctx *ctx);
 int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, int *fb_count,
@@ -137,7 +139,8 @@ struct DeviceGuard {
 int weights_job_from_args(mm_ctx *ctx, unsigned ops, int k, int m, int dim, int64_t N,
                           const double *d_pts, const double *d_normals,
                           const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
-                          int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job);
+                          int n_max, double *const *d_vals, int32_t *d_status, WeightsJob *job,
+                          bool wls = false);
 
 // Number of monomials of total degree <= m in dim variables: C(m+dim, dim).
 inline int mm_num_monomials(int dim, int m) {
