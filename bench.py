@@ -310,6 +310,39 @@ class DiskPipeline:
         self.weights_boundary(precision)
         self.apply()
 
+    def step_host(self, precision, h_pts, h_nrm, h_out, copy_stream, chunks=8):
+        """The same step with host inputs and outputs: points and normals
+        copied in, then the interior weights in row chunks, each chunk's three
+        value ranges copied to the pinned host arrays h_out on copy_stream
+        while the next chunk computes (the step ends when every copy has)."""
+        import torch
+        cur = torch.cuda.current_stream(self.pts.device)
+        self.pts.copy_(h_pts, non_blocking=True)
+        self.nrm.copy_(h_nrm, non_blocking=True)
+        self.knn()
+
+        def fetch(b, e):
+            ev = torch.cuda.Event()
+            ev.record(cur)
+            copy_stream.wait_event(ev)
+            lo, hi = int(self.rp_h[b]), int(self.rp_h[e])
+            with torch.cuda.stream(copy_stream):
+                for h, d in zip(h_out, (self.op, self.dx, self.dy)):
+                    h[lo:hi].copy_(d[lo:hi], non_blocking=True)
+
+        wi = DISK["interior"]
+        bounds = np.linspace(self.ib, self.ie, chunks + 1).astype(np.int64)
+        for b, e in zip(bounds[:-1], bounds[1:]):
+            self.ctx.rbffd_weights(wi["ops"], wi["k"], wi["m"], self.pts, self.rp, self.col,
+                                   [self.op, self.dx, self.dy], row_begin=int(b), row_end=int(e),
+                                   n_max=wi["n"], precision=precision, normals=self.nrm,
+                                   status=self.status)
+            fetch(b, e)
+        self.weights_boundary(precision)
+        fetch(self.bb, self.be)
+        self.apply()
+        cur.wait_stream(copy_stream)
+
 
 def timed_disk_steps(pipe, precision, steps, stream, flush):
     """Per-step CUDA-event times (L2 flushed between steps): whole step,
@@ -520,23 +553,28 @@ def run_disk(args, rk):
         h_pts = torch.from_numpy(ns.pts).pin_memory()
         h_nrm = torch.from_numpy(ns.normals).pin_memory()
         h_out = [torch.empty(pipe.nnz, dtype=torch.float64).pin_memory() for _ in range(3)]
+        copy_stream = torch.cuda.Stream(device)
+        pipe.step_host(P.FP32_IR, h_pts, h_nrm, h_out, copy_stream)
+        torch.cuda.synchronize()
         e_ms = []
         for _ in range(args.steps):
             flush.add_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            pipe.pts.copy_(h_pts, non_blocking=True)
-            pipe.nrm.copy_(h_nrm, non_blocking=True)
-            pipe.step(P.FP32_IR)
-            for h, d in zip(h_out, (pipe.op, pipe.dx, pipe.dy)):
-                h.copy_(d, non_blocking=True)
+            pipe.step_host(P.FP32_IR, h_pts, h_nrm, h_out, copy_stream)
             b.record(stream)
             b.synchronize()
             e_ms.append(a.elapsed_time(b))
         (e_tot,) = rk.max([float(np.sum(e_ms))])
         e2e = {"value": throughput(n_all, e_tot, args.steps), "unit": "nodes/s",
                "h2d_bytes_per_step": int((h_pts.numel() + h_nrm.numel()) * 8),
-               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in h_out))}
+               "d2h_bytes_per_step": int(sum(h.numel() * 8 for h in h_out)),
+               "overlap": "interior weights in 8 row chunks; each chunk's values copied to pinned "
+                          "host memory on a second stream while the next chunk computes"}
+        # the host copies must equal the device weights of the same step
+        for h, d in zip(h_out, (pipe.op, pipe.dx, pipe.dy)):
+            if not torch.equal(h, d.cpu()):
+                raise RuntimeError("host copy of the weights differs from the device arrays")
 
     wi = DISK["interior"]
     Ni = pipe.ie - pipe.ib
