@@ -27,6 +27,9 @@
  *   orc_spmv, orc_diffuse   Section 2.3.1 (explicit evaluation w^T u_I(i) and
  *                           explicit Euler, eq. exp-start..exp-end, interior
  *                           update with Dirichlet nodes held).
+ *   orc_diffuse_bc          the same with Neumann nodes: eq. exp-end, the
+ *                           discrete d/dn of the node set equal to g_n and
+ *                           solved for the node's own value.
  *   orc_project_lap         least-norm correction of given scaled Laplacian
  *                           weights onto the monomial rows Q^T w = l_q of
  *                           eq. rbf-system-aug.
@@ -454,6 +457,37 @@ void orc_spmv(int64_t nrows, const int64_t *row_ptr, const int32_t *col, const d
         for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) acc = acc + vals[p] * u[col[p]];
         y[i] = beta == 0.0 ? alpha * acc : alpha * acc + beta * y[i];
     }
+}
+
+/* Explicit steps with boundary kinds, eq. exp-start..exp-end, every update
+ * from the previous step's values: kind 0 (internal) u_i <- u_i + dt (L u)_i;
+ * kind 1 (Dirichlet) keeps u_i; kind 2 (Neumann) takes the node's row as its
+ * d/dn weights (centre first) and sets
+ *     u_i <- (g_i - sum_{j >= 2} w_ij u_j) / w_i1,
+ * g = NULL meaning g_i = 0. */
+int orc_diffuse_bc(int64_t nrows, const int64_t *row_ptr, const int32_t *col, const double *vals,
+                   const uint8_t *kind, const double *g, double dt, int steps, double *u)
+{
+    double *nu = (double *)malloc(sizeof(double) * (size_t)(nrows > 0 ? nrows : 1));
+    if (!nu) return ORC_NOMEM;
+    for (int t = 0; t < steps; ++t) {
+        for (int64_t i = 0; i < nrows; ++i) {
+            if (kind[i] == 1) {
+                nu[i] = u[i];
+            } else if (kind[i] == 2) {
+                double s = 0.0;
+                for (int64_t p = row_ptr[i] + 1; p < row_ptr[i + 1]; ++p) s = s + vals[p] * u[col[p]];
+                nu[i] = ((g ? g[i] : 0.0) - s) / vals[row_ptr[i]];
+            } else {
+                double acc = 0.0;
+                for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) acc = acc + vals[p] * u[col[p]];
+                nu[i] = u[i] + dt * acc;
+            }
+        }
+        memcpy(u, nu, sizeof(double) * (size_t)nrows);
+    }
+    free(nu);
+    return ORC_OK;
 }
 
 /* Explicit Euler steps u <- u + dt * L u on rows with fixed[i] == 0; rows with

@@ -75,6 +75,9 @@ def _load():
     lib.orc_diffuse.argtypes = [i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, dbl,
                                 C.c_int, C.c_void_p]
     lib.orc_diffuse.restype = C.c_int
+    lib.orc_diffuse_bc.argtypes = [i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   dbl, C.c_int, C.c_void_p]
+    lib.orc_diffuse_bc.restype = C.c_int
     lib.orc_project_lap.argtypes = [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                     C.c_void_p, C.c_void_p]
     lib.orc_project_lap.restype = C.c_int
@@ -237,6 +240,40 @@ def diffuse(row_ptr, col, vals, fixed, dt, steps, u):
     if rc != OK:
         raise MemoryError("orc_diffuse")
     return u
+
+
+def diffuse_bc(row_ptr, col, vals, kind, g, dt, steps, u):
+    """Explicit steps with internal (0), Dirichlet (1) and Neumann (2) rows,
+    eq. exp-start..exp-end (see orc_diffuse_bc); g [nrows] or None."""
+    lib = _load()
+    row_ptr = _c(row_ptr, np.int64)
+    col = _c(col, np.int32)
+    vals = _c(vals, np.float64)
+    kind = _c(kind, np.uint8)
+    gg = None if g is None else _c(g, np.float64)
+    u = np.array(u, dtype=np.float64)
+    rc = lib.orc_diffuse_bc(len(row_ptr) - 1, _ptr(row_ptr), _ptr(col), _ptr(vals), _ptr(kind),
+                            _ptr(gg), dt, steps, _ptr(u))
+    if rc != OK:
+        raise MemoryError("orc_diffuse_bc")
+    return u
+
+
+def combine_operators(row_ptr, terms, coefs, rows=None):
+    """General second-order operator from derivative weights (eq. gen-op):
+    w_L[e] = sum_t a_t(i) w_t[e] for every entry e of row i; coefs[t] is a
+    per-node array [nrows] or None (coefficient 1).  Rows outside ``rows``
+    (a (begin, end) pair) are zero."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    nrows = len(row_ptr) - 1
+    rb, re = (0, nrows) if rows is None else rows
+    row_of = np.repeat(np.arange(nrows), np.diff(row_ptr))
+    out = np.zeros(int(row_ptr[-1]))
+    sel = (row_of >= rb) & (row_of < re)
+    for w, a in zip(terms, coefs):
+        c = np.ones(nrows) if a is None else np.asarray(a, dtype=np.float64)
+        out[sel] += c[row_of[sel]] * np.asarray(w)[sel]
+    return out
 
 
 # ------------------------------------------------- projection / residual check
