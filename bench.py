@@ -576,6 +576,29 @@ def run_disk(args, rk):
             if not torch.equal(h, d.cpu()):
                 raise RuntimeError("host copy of the weights differs from the device arrays")
 
+    # general second-order operator (eq. gen-op) from the three weight arrays
+    # with per-node coefficients, timed alone: HBM-bound, (terms + 1) x 8 bytes
+    # per nonzero plus the coefficients and row pointers
+    coefs = [torch.ones(ns.N, dtype=torch.float64, device=pipe.pts.device) * c for c in (1.0, 0.5, -0.25)]
+    wl = torch.empty_like(pipe.op)
+    cm = []
+    for t in range(max(3, args.warmup) + args.steps):
+        flush.add_(1.0)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.combine_operators(pipe.rp, pipe.col, [pipe.op, pipe.dx, pipe.dy], coefs, wl)
+        z.record(stream)
+        z.synchronize()
+        if t >= max(3, args.warmup):
+            cm.append(a.elapsed_time(z))
+    comb_bytes = 4 * 8 * pipe.nnz + 3 * 8 * ns.N + 8 * (ns.N + 1)
+    hbm = peaks_file().get("hbm_gbs")
+    comb_gbs = comb_bytes / (float(np.mean(cm)) * 1e-3) / 1e9
+    comb_roof = {"bound": "hbm", "kernel": "k_combine (3 weight arrays, per-node coefficients)",
+                 "achieved": comb_gbs, "unit": "GB/s", "peak": hbm, "frac": comb_gbs / hbm if hbm else None,
+                 "ms": float(np.mean(cm)), "bytes": comb_bytes,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+
     wi = DISK["interior"]
     Ni = pipe.ie - pipe.ib
     f32 = mixed_fp32_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
@@ -624,6 +647,7 @@ def run_disk(args, rk):
             "fp64_equivalent": fp64_equiv,
             "speedup_vs_fp64_plain": ms64 / ms, "weights_ms": float(np.mean(wts)),
             "fallback_fraction": fallback, "roofline": roof, "roofline_spmv": spmv_roof,
+            "roofline_combine": comb_roof,
             "peaks_measured": {"fp64_flops": fp64_peak, "fp32_flops": fp32_peak},
             "e2e": e2e, "clocks": clk, "gpu_launches": DISK_LAUNCHES_PER_STEP * args.steps}
     if rk.rank == 0 and not args.no_error:

@@ -335,6 +335,43 @@ int mm_apply_operator(mm_ctx *ctx, const mm_csr_pattern *stencils, const double 
 int mm_diffuse(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
                const uint8_t *d_fixed, double dt, int steps, double *d_u, double *d_work);
 
+/* Row kinds of mm_diffuse_bc */
+#define MM_ROW_INTERNAL 0
+#define MM_ROW_DIRICHLET 1
+#define MM_ROW_NEUMANN 2
+
+/*
+ * mm_diffuse with Neumann nodes (eq. exp-end of Section 2.3.1).  Every step
+ * uses the previous step's field:
+ *   d_kind[i] == MM_ROW_INTERNAL:  u_i <- u_i + dt (L u)_i
+ *   d_kind[i] == MM_ROW_NEUMANN:   row i of the operator holds the node's
+ *       d/dn weights, centre first (as mm_rbffd_weights writes them), and
+ *       u_i <- (g_i - sum_{j >= 2} w_ij u_{I(i,j)}) / w_i1
+ *   any other kind (MM_ROW_DIRICHLET): u_i kept.
+ * d_g [nrows] Neumann data g_n (NULL: 0), constant in time; it must not alias
+ * d_u or d_work.  A centre weight of 0 gives a non-finite value.  The update
+ * divides by the centre d/dn weight, so with one-sided stencils whose centre
+ * weight is small against the others, coupled Neumann nodes amplify errors
+ * from step to step.  Errors: as mm_diffuse.
+ */
+int mm_diffuse_bc(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+                  const uint8_t *d_kind, const double *d_g, double dt, int steps, double *d_u,
+                  double *d_work);
+
+/*
+ * General second-order operator from derivative weights (eq. gen-op,
+ * Section 3.3): for the rows i in [row_begin, row_end),
+ *     d_out[e] = sum_t a_t(i) * d_terms[t][e]   for each entry e of row i,
+ * a_t(i) = d_coef[t][i] (per-node coefficient, [nrows]) or 1 where d_coef (a
+ * HOST array of nterms device pointers, or NULL for all 1) has NULL.  The
+ * terms are value arrays of the same CSR pattern, e.g. the weights of d/dx_a
+ * and d2/dx_a dx_b; d_out may be one of them.  Entries outside the rows are
+ * not written.  Requirements: 1 <= nterms <= 10.  Errors: MM_EBADARG, MM_ECUDA.
+ */
+int mm_combine_operators(mm_ctx *ctx, const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
+                         int nterms, const double *const *d_terms, const double *const *d_coef,
+                         double *d_out);
+
 /* ------------------------------------------------- learned surrogate (MLP) */
 /*
  * A GELU multilayer perceptron n_in -> 256 -> 256 -> 256 -> n_out that maps

@@ -26,6 +26,7 @@ WIDE_FF, WIDE_FP64 = 0, 1
 MLP_FUSED, MLP_LAYERED = 0, 1
 GJ_AUTO, GJ_SHARED = 0, 1
 SCALE_FARTHEST, SCALE_NEAREST = 0, 1
+ROW_INTERNAL, ROW_DIRICHLET, ROW_NEUMANN = 0, 1, 2
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
            "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
@@ -34,7 +35,8 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_tile_table_load", "mm_mlp_create", "mm_mlp_destroy", "mm_mlp_num_params",
            "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_output_scaling",
            "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
-           "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights"]
+           "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights", "mm_diffuse_bc",
+           "mm_combine_operators"]
 
 
 class KnnRange(C.Structure):
@@ -123,6 +125,9 @@ def load():
                                                    C.c_int, vp, vp, vp]
         lib.mm_apply_operator.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, dbl, vp]
         lib.mm_diffuse.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, dbl, C.c_int, vp, vp]
+        lib.mm_diffuse_bc.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, dbl, C.c_int, vp, vp]
+        lib.mm_combine_operators.argtypes = [vp, C.POINTER(CsrPattern), i64, i64, C.c_int, C.POINTER(vp),
+                                             C.POINTER(vp), vp]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
         for name in EXPORTS:
             if name not in ("mm_ctx_destroy", "mm_last_error", "mm_mlp_destroy",
@@ -355,6 +360,46 @@ class Context:
         pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
         self._check(self._lib.mm_diffuse(self._h, C.byref(pat), _ptr(vals), _ptr(fixed),
                                          float(dt), int(steps), _ptr(u), _ptr(work)))
+
+    def diffuse_bc(self, row_ptr, col, vals, kind, g, dt, steps, u, work):
+        """mm_diffuse_bc: kind [nrows] uint8 (ROW_INTERNAL / ROW_DIRICHLET /
+        ROW_NEUMANN), g [nrows] float64 Neumann data or None."""
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        _dev(vals, "vals", torch.float64)
+        _dev(kind, "kind", torch.uint8)
+        if g is not None:
+            _dev(g, "g", torch.float64)
+        _dev(u, "u", torch.float64)
+        _dev(work, "work", torch.float64)
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        self._check(self._lib.mm_diffuse_bc(self._h, C.byref(pat), _ptr(vals), _ptr(kind), _ptr(g),
+                                            float(dt), int(steps), _ptr(u), _ptr(work)))
+
+    def combine_operators(self, row_ptr, col, terms, coefs, out, row_begin: int = 0,
+                          row_end: int | None = None):
+        """mm_combine_operators: out = sum_t coefs[t][row] * terms[t] (coefs[t]
+        None means 1; coefs None means all 1)."""
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        _dev(out, "out", torch.float64)
+        for t in terms:
+            _dev(t, "terms", torch.float64)
+        if coefs is not None:
+            if len(coefs) != len(terms):
+                raise MMError("one coefficient array (or None) per term expected")
+            for a in coefs:
+                if a is not None:
+                    _dev(a, "coefs", torch.float64)
+        nrows = row_ptr.numel() - 1
+        if row_end is None:
+            row_end = nrows
+        pat = CsrPattern(nrows, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        tp = (C.c_void_p * max(1, len(terms)))(*[t.data_ptr() for t in terms])
+        cp = None if coefs is None else (C.c_void_p * len(coefs))(
+            *[None if a is None else a.data_ptr() for a in coefs])
+        self._check(self._lib.mm_combine_operators(self._h, C.byref(pat), row_begin, row_end, len(terms),
+                                                   tp, cp, _ptr(out)))
 
     def measure_fma_peak(self, which: int) -> float:
         out = C.c_double()

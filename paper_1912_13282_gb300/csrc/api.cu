@@ -318,7 +318,40 @@ int mm_diffuse(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals
         return mm_fail(ctx, MM_EBADARG, "NULL argument");
     if (d_u == d_work && stencils->nrows > 0) return mm_fail(ctx, MM_EBADARG, "d_work aliases d_u");
     DeviceGuard g(ctx);
-    return diffuse_launch(ctx, stencils, d_vals, d_fixed, dt, steps, d_u, d_work);
+    return diffuse_launch(ctx, stencils, d_vals, d_fixed, nullptr, 0, dt, steps, d_u, d_work);
+}
+
+int mm_diffuse_bc(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+                  const uint8_t *d_kind, const double *d_g, double dt, int steps, double *d_u,
+                  double *d_work) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (!stencils || !stencils->d_row_ptr || !stencils->d_col || stencils->nrows < 0)
+        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
+    if (steps < 0) return mm_fail(ctx, MM_EBADARG, "steps < 0");
+    if (stencils->nrows > 0 && (!d_vals || !d_kind || !d_u || !d_work))
+        return mm_fail(ctx, MM_EBADARG, "NULL argument");
+    if (d_u == d_work && stencils->nrows > 0) return mm_fail(ctx, MM_EBADARG, "d_work aliases d_u");
+    if (d_g && (d_g == d_u || d_g == d_work)) return mm_fail(ctx, MM_EBADARG, "d_g aliases d_u or d_work");
+    DeviceGuard g(ctx);
+    return diffuse_launch(ctx, stencils, d_vals, d_kind, d_g, 1, dt, steps, d_u, d_work);
+}
+
+int mm_combine_operators(mm_ctx *ctx, const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end,
+                         int nterms, const double *const *d_terms, const double *const *d_coef,
+                         double *d_out) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (!stencils || !stencils->d_row_ptr || stencils->nrows < 0)
+        return mm_fail(ctx, MM_EBADARG, "bad stencil pattern");
+    if (row_begin < 0 || row_end < row_begin || row_end > stencils->nrows)
+        return mm_fail(ctx, MM_EBADARG, "row range out of [0, nrows]");
+    if (nterms < 1 || nterms > 10) return mm_fail(ctx, MM_EBADARG, "nterms must be in [1, 10]");
+    if (!d_terms || !d_out) return mm_fail(ctx, MM_EBADARG, "NULL argument");
+    for (int t = 0; t < nterms; ++t)
+        if (!d_terms[t]) return mm_fail(ctx, MM_EBADARG, "d_terms[%d] is NULL", t);
+    DeviceGuard g(ctx);
+    return combine_launch(ctx, stencils, row_begin, row_end, nterms, d_terms, d_coef, d_out);
 }
 
 int mm_measure_fma_peak(mm_ctx *ctx, int which, double *flops_per_s) {

@@ -119,8 +119,10 @@ int weights_launch_scratch(mm_ctx *ctx, const WeightsJob &job, int precision, in
                            int *fb_list);
 int spmv_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const double *u,
                 double alpha, double beta, double *y);
-int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals,
-                   const uint8_t *fixed, double dt, int steps, double *u, double *work);
+int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const uint8_t *fixed,
+                   const double *g, int neumann, double dt, int steps, double *u, double *work);
+int combine_launch(mm_ctx *ctx, const mm_csr_pattern *p, int64_t row_begin, int64_t row_end, int nterms,
+                   const double *const *terms, const double *const *coefs, double *out);
 int peaks_measure(mm_ctx *ctx, int which, double *flops_per_s);
 
 // Makes the context's device current for the duration of a call.

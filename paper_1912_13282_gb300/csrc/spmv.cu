@@ -1,6 +1,9 @@
 // Operator application (Section 2.3.1 of the paper, explicit evaluation
-// w^T u_I(i)): CSR SpMV y = alpha L u + beta y, and explicit Euler steps
-// u <- u + dt L u on free rows (eq. exp-start .. exp-end, Dirichlet rows held).
+// w^T u_I(i)): CSR SpMV y = alpha L u + beta y, explicit Euler steps
+// u <- u + dt L u on internal rows (eq. exp-start .. exp-end: Dirichlet rows
+// held, Neumann rows solved from their own d/dn row), and the general
+// second-order operator as a per-node combination of derivative weights
+// (eq. gen-op).
 //
 // A group of G lanes (G a power of two, chosen from the mean row length)
 // handles a row: the lanes read consecutive value/column entries of the row
@@ -75,11 +78,16 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t nrows, const int64_t *__re
     }
 }
 
+// kind[i]: 0 internal (u + dt L u), 2 with `neumann` set: the row holds the
+// node's d/dn weights, centre first, and u_i <- (g_i - sum_{j>=2} w_ij u_j) /
+// w_i1 (eq. exp-end; g may be NULL for 0); any other value keeps u_i.  All
+// from the previous step's field.
 template <int G>
 __global__ void __launch_bounds__(256) k_diffuse_step(int64_t nrows, const int64_t *__restrict__ rp,
                                                       const int32_t *__restrict__ col,
                                                       const double *__restrict__ val,
-                                                      const uint8_t *__restrict__ fixed,
+                                                      const uint8_t *__restrict__ kind,
+                                                      const double *__restrict__ g, int neumann,
                                                       const double *__restrict__ u, double dt,
                                                       double *__restrict__ unew) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -92,8 +100,49 @@ __global__ void __launch_bounds__(256) k_diffuse_step(int64_t nrows, const int64
         for (int r = 0; r < RB; ++r)
             if (r % G == sub && base + r < nrows) {
                 const int64_t row = base + r;
-                unew[row] = fixed[row] ? u[row] : fma(dt, acc[r], u[row]);
+                const int k = kind[row];
+                double v = u[row];
+                if (k == 0) {
+                    v = fma(dt, acc[r], v);
+                } else if (k == 2 && neumann) {
+                    const double w1 = __ldg(val + __ldg(rp + row));   // centre weight
+                    const double rest = fma(-w1, v, acc[r]);          // sum over the other nodes
+                    v = ((g ? g[row] : 0.0) - rest) / w1;
+                }
+                unew[row] = v;
             }
+    }
+}
+
+// General second-order operator (eq. gen-op): out[e] = sum_t a_t(i) term_t[e]
+// for the entries e of row i, a_t(i) = coef_t[i] (1 if coef_t is NULL).  G
+// lanes per row read consecutive entries; bound by HBM traffic ((T + 1) x 8
+// bytes per nonzero).
+constexpr int kMaxTerms = 10;
+struct CombineArgs {
+    int nterms;
+    const double *term[kMaxTerms];
+    const double *coef[kMaxTerms];
+};
+
+template <int G>
+__global__ void __launch_bounds__(256) k_combine(int64_t row_begin, int64_t row_end, const int64_t *__restrict__ rp,
+                                                 const __grid_constant__ CombineArgs A, double *out) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int sub = threadIdx.x & (G - 1);
+    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+    for (int64_t row = row_begin + tid / G; row < row_end; row += ngroups) {
+        double a[kMaxTerms];
+#pragma unroll
+        for (int t = 0; t < kMaxTerms; ++t) a[t] = t < A.nterms ? (A.coef[t] ? __ldg(A.coef[t] + row) : 1.0) : 0.0;
+        const int64_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
+        for (int64_t p = b + sub; p < e; p += G) {
+            double s = 0.0;
+#pragma unroll
+            for (int t = 0; t < kMaxTerms; ++t)
+                if (t < A.nterms) s = fma(a[t], A.term[t][p], s);
+            out[p] = s;
+        }
     }
 }
 
@@ -125,8 +174,25 @@ int spmv_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const 
     return MM_OK;
 }
 
+int combine_launch(mm_ctx *ctx, const mm_csr_pattern *p, int64_t row_begin, int64_t row_end, int nterms,
+                   const double *const *terms, const double *const *coefs, double *out) {
+    if (row_end <= row_begin) return MM_OK;
+    CombineArgs A{};
+    A.nterms = nterms;
+    for (int t = 0; t < nterms; ++t) {
+        A.term[t] = terms[t];
+        A.coef[t] = coefs ? coefs[t] : nullptr;
+    }
+    const int G = 4;
+    const int64_t rows = row_end - row_begin;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * G + 255) / 256, (int64_t)ctx->num_sms * 8));
+    k_combine<G><<<blocks, 256, 0, ctx->stream>>>(row_begin, row_end, p->d_row_ptr, A, out);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
 int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const uint8_t *fixed,
-                   double dt, int steps, double *u, double *work) {
+                   const double *g, int neumann, double dt, int steps, double *u, double *work) {
     if (p->nrows == 0 || steps <= 0) return MM_OK;
     const int G = group_for(p);
     const int blocks = grid_for(ctx, p->nrows, G);
@@ -134,8 +200,8 @@ int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, con
     double *src = u, *dst = work;
     for (int t = 0; t < steps; ++t) {
         switch (G) {
-            case 8: k_diffuse_step<8><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, src, dt, dst); break;
-            default: k_diffuse_step<4><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, src, dt, dst); break;
+            case 8: k_diffuse_step<8><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, g, neumann, src, dt, dst); break;
+            default: k_diffuse_step<4><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, g, neumann, src, dt, dst); break;
         }
         MM_LAUNCH_CHECK(ctx);
         double *t2 = src; src = dst; dst = t2;
