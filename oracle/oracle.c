@@ -30,6 +30,11 @@
  *   orc_diffuse_bc          the same with Neumann nodes: eq. exp-end, the
  *                           discrete d/dn of the node set equal to g_n and
  *                           solved for the node's own value.
+ *   orc_ilu0, orc_ilu0_solve, orc_bicgstab
+ *                           the implicit solve of Section 2.3.2: BiCGSTAB
+ *                           (van der Vorst) with an incomplete-LU
+ *                           preconditioner of the ILUT family, here ILU(0)
+ *                           (the pattern of A, no dropping).
  *   orc_project_lap         least-norm correction of given scaled Laplacian
  *                           weights onto the monomial rows Q^T w = l_q of
  *                           eq. rbf-system-aug.
@@ -488,6 +493,133 @@ int orc_diffuse_bc(int64_t nrows, const int64_t *row_ptr, const int32_t *col, co
     }
     free(nu);
     return ORC_OK;
+}
+
+/* ILU(0) in place on a CSR matrix whose rows have sorted columns and a
+ * diagonal entry: afterwards the strictly lower part holds L (unit diagonal
+ * implied) and the rest U, with (L U)_ij = A_ij for every (i, j) of the
+ * pattern (row-by-row elimination, updates outside the pattern dropped).
+ * diag[i] receives the position of (i, i).  ORC_BADARG: a diagonal entry is
+ * missing; ORC_SINGULAR: a zero pivot. */
+int orc_ilu0(int64_t n, const int64_t *rp, const int32_t *col, double *val, int64_t *diag)
+{
+    int64_t *where = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!where) return ORC_NOMEM;
+    for (int64_t i = 0; i < n; ++i) where[i] = -1;
+    int rc = ORC_OK;
+    for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+        diag[i] = -1;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            where[col[p]] = p;
+            if (col[p] == i) diag[i] = p;
+        }
+        if (diag[i] < 0) rc = ORC_BADARG;
+        for (int64_t p = rp[i]; rc == ORC_OK && p < rp[i + 1] && col[p] < i; ++p) {
+            const int64_t k = col[p];
+            if (val[diag[k]] == 0.0) { rc = ORC_SINGULAR; break; }
+            const double lik = val[p] / val[diag[k]];
+            val[p] = lik;
+            for (int64_t q = diag[k] + 1; q < rp[k + 1]; ++q) {
+                const int64_t w = where[col[q]];
+                if (w >= 0) val[w] = val[w] - lik * val[q];
+            }
+        }
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) where[col[p]] = -1;
+        if (rc == ORC_OK && val[diag[i]] == 0.0) rc = ORC_SINGULAR;
+    }
+    free(where);
+    return rc;
+}
+
+/* x = (L U)^-1 b with the factors of orc_ilu0 (forward, then back substitution). */
+void orc_ilu0_solve(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                    const int64_t *diag, const double *b, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int64_t p = rp[i]; p < diag[i]; ++p) s = s - val[p] * x[col[p]];
+        x[i] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int64_t p = diag[i] + 1; p < rp[i + 1]; ++p) s = s - val[p] * x[col[p]];
+        x[i] = s / val[diag[i]];
+    }
+}
+
+static void orc_csr_mv(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                       const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s = s + val[p] * x[col[p]];
+        y[i] = s;
+    }
+}
+
+static double orc_dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = s + a[i] * b[i];
+    return s;
+}
+
+/* BiCGSTAB (van der Vorst 1992) for A x = b, preconditioned by the ILU(0)
+ * factors fval/diag of the same pattern (M = L U; NULL: none), x holding the
+ * initial guess on entry.  Stops when ||b - A x||_2 <= tol ||b||_2 (the
+ * recursively updated residual), or after maxit iterations.  *iters and
+ * *relres receive the iterations taken and the final relative residual.
+ * Returns ORC_OK when converged, ORC_SINGULAR on a breakdown or no
+ * convergence. */
+int orc_bicgstab(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                 const double *fval, const int64_t *diag, const double *b, double *x,
+                 double tol, int maxit, int *iters, double *relres)
+{
+    double *w = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 8);
+    if (!w) return ORC_NOMEM;
+    double *r = w, *rh = w + n, *p = w + 2 * n, *v = w + 3 * n, *ph = w + 4 * n, *s = w + 5 * n,
+           *sh = w + 6 * n, *t = w + 7 * n;
+    orc_csr_mv(n, rp, col, val, x, t);
+    for (int64_t i = 0; i < n; ++i) {
+        r[i] = b[i] - t[i];
+        rh[i] = r[i];
+        p[i] = v[i] = 0.0;
+    }
+    const double nb = sqrt(orc_dot(n, b, b));
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    double res = sqrt(orc_dot(n, r, r)) / (nb > 0 ? nb : 1.0);
+    int it = 0, rc = ORC_SINGULAR;
+    if (res <= tol) rc = ORC_OK;
+    while (rc != ORC_OK && it < maxit) {
+        ++it;
+        const double rho1 = orc_dot(n, rh, r);
+        if (rho1 == 0.0 || omega == 0.0) break;
+        const double beta = (rho1 / rho) * (alpha / omega);
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        if (fval) orc_ilu0_solve(n, rp, col, fval, diag, p, ph);
+        else memcpy(ph, p, sizeof(double) * (size_t)n);
+        orc_csr_mv(n, rp, col, val, ph, v);
+        const double rv = orc_dot(n, rh, v);
+        if (rv == 0.0) break;
+        alpha = rho1 / rv;
+        for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+        if (fval) orc_ilu0_solve(n, rp, col, fval, diag, s, sh);
+        else memcpy(sh, s, sizeof(double) * (size_t)n);
+        orc_csr_mv(n, rp, col, val, sh, t);
+        const double tt = orc_dot(n, t, t);
+        omega = tt > 0.0 ? orc_dot(n, t, s) / tt : 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] = x[i] + alpha * ph[i] + omega * sh[i];
+            r[i] = s[i] - omega * t[i];
+        }
+        rho = rho1;
+        res = sqrt(orc_dot(n, r, r)) / (nb > 0 ? nb : 1.0);
+        if (res <= tol) rc = ORC_OK;
+    }
+    *iters = it;
+    *relres = res;
+    free(w);
+    return rc;
 }
 
 /* Explicit Euler steps u <- u + dt * L u on rows with fixed[i] == 0; rows with

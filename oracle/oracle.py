@@ -78,6 +78,15 @@ def _load():
     lib.orc_diffuse_bc.argtypes = [i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    dbl, C.c_int, C.c_void_p]
     lib.orc_diffuse_bc.restype = C.c_int
+    lib.orc_ilu0.argtypes = [i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_ilu0.restype = C.c_int
+    lib.orc_ilu0_solve.argtypes = [i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]
+    lib.orc_ilu0_solve.restype = None
+    lib.orc_bicgstab.argtypes = [i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, dbl, C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(dbl)]
+    lib.orc_bicgstab.restype = C.c_int
     lib.orc_project_lap.argtypes = [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                     C.c_void_p, C.c_void_p]
     lib.orc_project_lap.restype = C.c_int
@@ -257,6 +266,58 @@ def diffuse_bc(row_ptr, col, vals, kind, g, dt, steps, u):
     if rc != OK:
         raise MemoryError("orc_diffuse_bc")
     return u
+
+
+def sort_rows(row_ptr, col, vals):
+    """The same CSR matrix with the columns of every row in ascending order."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    row_of = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
+    order = np.lexsort((col, row_of))
+    return row_ptr.copy(), col[order].astype(np.int32), np.asarray(vals, dtype=np.float64)[order]
+
+
+def ilu0(row_ptr, col, vals):
+    """ILU(0) factors of a CSR matrix with sorted rows and a diagonal in every
+    row: (factor values in the same pattern, diagonal positions)."""
+    lib = _load()
+    row_ptr = _c(row_ptr, np.int64)
+    col = _c(col, np.int32)
+    f = np.array(vals, dtype=np.float64)
+    n = len(row_ptr) - 1
+    diag = np.zeros(n, dtype=np.int64)
+    rc = lib.orc_ilu0(n, _ptr(row_ptr), _ptr(col), _ptr(f), _ptr(diag))
+    if rc != OK:
+        raise ValueError(f"orc_ilu0 rc={rc}")
+    return f, diag
+
+
+def ilu0_solve(row_ptr, col, fvals, diag, b):
+    lib = _load()
+    row_ptr = _c(row_ptr, np.int64)
+    col = _c(col, np.int32)
+    fvals = _c(fvals, np.float64)
+    diag = _c(diag, np.int64)
+    b = _c(b, np.float64)
+    x = np.zeros(len(b))
+    lib.orc_ilu0_solve(len(b), _ptr(row_ptr), _ptr(col), _ptr(fvals), _ptr(diag), _ptr(b), _ptr(x))
+    return x
+
+
+def bicgstab(row_ptr, col, vals, b, x0=None, precondition=True, tol=1e-12, maxit=5000):
+    """BiCGSTAB with ILU(0) (or no) preconditioning on a CSR matrix with
+    sorted rows: (x, converged, iterations, relative residual)."""
+    lib = _load()
+    row_ptr = _c(row_ptr, np.int64)
+    col = _c(col, np.int32)
+    vals = _c(vals, np.float64)
+    b = _c(b, np.float64)
+    x = np.zeros(len(b)) if x0 is None else np.array(x0, dtype=np.float64)
+    f, diag = ilu0(row_ptr, col, vals) if precondition else (None, None)
+    it, res = C.c_int(0), C.c_double(0.0)
+    rc = lib.orc_bicgstab(len(b), _ptr(row_ptr), _ptr(col), _ptr(vals), _ptr(f), _ptr(diag), _ptr(b),
+                          _ptr(x), tol, maxit, C.byref(it), C.byref(res))
+    return x, rc == OK, it.value, res.value
 
 
 def combine_operators(row_ptr, terms, coefs, rows=None):
