@@ -1,8 +1,8 @@
 // Device-side building blocks of the RBF-FD weights kernels (one warp per
 // stencil): stencil loading and scaling, assembly of the augmented system of
 // Section 2.2.2 (eq. rbf-system-aug), the FP64 partial-pivot LU, the FP32
-// implicit-pivot LU and solves, and the per-row FP64 and FP32+refinement
-// solvers.  Included by the per-class kernels (rbffd.cu) and the persistent
+// Gauss-Jordan inverse (shared-memory and register forms) and its products,
+// the per-row FP64 and FP32+refinement solvers.  Included by the per-class kernels (rbffd.cu) and the persistent
 // batched kernel (batched.cu); each translation unit gets its own copy of the
 // constant monomial table and uploads it at context creation.
 #pragma once
