@@ -2,9 +2,9 @@
 // paper): a GELU multilayer perceptron 2n -> 256 -> 256 -> 256 -> n on the
 // scaled stencil offsets, BF16 weights/activations with FP32 accumulation on
 // the tensor cores (mma.sync m16n8k16), trained on weights the method itself
-// produces.  Its predictions are projected in FP64 onto the monomial rows
+// produces.  Its predictions are projected (double-FP32, or FP64) onto the rows
 // Q^T w = l_q of the augmented system (Section 2.2.2, eq. rbf-system-aug), then
-// checked against the remaining rows' residual; rejected stencils get the FP64 solve.
+// checked against the remaining rows' residual; rejected stencils get a solve.
 //
 // Layout: feature width padded to 64, outputs to 32 (zero weights and inputs in
 // the padding), hidden width 256, 3 hidden layers.  Parameters are FP32
