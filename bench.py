@@ -200,6 +200,18 @@ def mixed_fp32_flops(n, l, R, dim, k, residuals=2):
     return gj + applies + 15 * terms + assembly
 
 
+def method_flops(n, l, R):
+    """The method's algorithmic flops for one stencil, whatever the solver:
+    an LU of the M x M augmented matrix ((2/3) M^3), forward and back
+    substitution for R right-hand sides (2 R M^2) and the assembly (8 flops
+    per node pair for the distance power, 4 per entry of Q, 6 per node and
+    operator for the right-hand side): (2/3) M^3 + 2 R M^2 + 8 n(n-1)/2 +
+    4 n l + 6 n R.  The same count serves the FP64 and the FP32 + refinement
+    forms, so their roofline fractions compare the same work."""
+    M = n + l
+    return 2.0 * M ** 3 / 3 + 2 * R * M * M + 8 * n * (n - 1) / 2 + 4 * n * l + 6 * n * R
+
+
 def fp64_solve_flops(n, l, R, dim, k):
     """Algorithmic FP64 flops of the plain solve: assembly, LU of the M x M
     augmented matrix applied to R right-hand sides, back substitution."""
@@ -347,9 +359,10 @@ class DiskPipeline:
 def timed_disk_steps(pipe, precision, steps, stream, flush):
     """Per-step CUDA-event times (L2 flushed between steps): whole step,
     weights, and the dominant launch (interior weights); the operator
-    applications' times are left in timed_disk_steps.apply_ms."""
+    applications' and the kNN's times are left in timed_disk_steps.apply_ms
+    and timed_disk_steps.knn_ms."""
     import torch
-    tot, wts, dom, app = [], [], [], []
+    tot, wts, dom, app, kn = [], [], [], [], []
     for _ in range(steps):
         flush.add_(1.0)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -367,7 +380,9 @@ def timed_disk_steps(pipe, precision, steps, stream, flush):
         wts.append(ev[1].elapsed_time(ev[3]))
         dom.append(ev[1].elapsed_time(ev[2]))
         app.append(ev[3].elapsed_time(ev[4]))
+        kn.append(ev[0].elapsed_time(ev[1]))
     timed_disk_steps.apply_ms = np.array(app)
+    timed_disk_steps.knn_ms = np.array(kn)
     return np.array(tot), np.array(wts), np.array(dom)
 
 
@@ -530,6 +545,7 @@ def run_disk(args, rk):
     torch.cuda.synchronize()
     tot, wts, dom = timed_disk_steps(pipe, P.FP32_IR, args.steps, stream, flush)
     apply_ms = float(np.median(timed_disk_steps.apply_ms))
+    knn_ms = float(np.mean(timed_disk_steps.knn_ms))
     torch.cuda.synchronize()
     # the same chosen form with native FP64 refinement residuals (MM_WIDE_FP64)
     ctx.set_option(P.binding.OPT_WIDE, P.binding.WIDE_FP64)
@@ -601,20 +617,29 @@ def run_disk(args, rk):
 
     wi = DISK["interior"]
     Ni = pipe.ie - pipe.ib
-    f32 = mixed_fp32_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
+    alg = method_flops(wi["n"], 15, 3) * Ni
+    issued = mixed_fp32_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
     dom_ms = float(np.mean(dom))
-    achieved = f32 / (dom_ms * 1e-3)
+    achieved = alg / (dom_ms * 1e-3)
     traffic = stored_traffic("k_weights_mixed<2,2,3,40>")
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak,
             "traffic": None if traffic is None else traffic["bytes_per_row"] * Ni,
             "kernel": "k_weights_mixed<2,2,3,40> (interior rows; FP32 Gauss-Jordan inverse with the "
                       "rows in registers + double-FP32 refinement)",
-            "algorithmic": "FP32 flops per interior stencil: inverse 2M^3, products with it, "
-                           "compensated residuals, double-FP32 assembly (bench.mixed_fp32_flops)",
+            "algorithmic": "the method's flops per interior stencil, (2/3)M^3 + 2RM^2 + 8n(n-1)/2 + 4nl "
+                           "+ 6nR = %.0f (M=40, R=3, n=25, l=15) x %d rows per launch (bench.method_flops)"
+                           % (method_flops(wi["n"], 15, 3), Ni),
+            "issued_flops": issued,
+            "issued_tflops": issued / (dom_ms * 1e-3) / 1e12,
+            "issued_note": "FP32 flops the implementation executes (explicit inverse 2M^3, products with "
+                           "it, 15-flop compensated residual terms, double-FP32 assembly; "
+                           "bench.mixed_fp32_flops); not the method's work",
+            "frac_of_fp64_peak": achieved / fp64_peak,
+            "ms": dom_ms, "units": Ni,
             "peak_source": "FP32 FMA peak measured in this run (mm_measure_fma_peak); "
                            "MEASURED_PEAKS.json has no FP32 CUDA-core figure"}
-    f64_plain = fp64_solve_flops(wi["n"], 15, 3, 2, wi["k"]) * Ni
+    f64_plain = method_flops(wi["n"], 15, 3) * Ni
     # operator application (3 SpMVs, the last with beta = 1): values and column
     # indices once, row pointers, x and y once per row (algorithmic bytes)
     N = ns.N
@@ -625,9 +650,20 @@ def run_disk(args, rk):
                  "peak": hbm, "frac": (spmv_bytes / (apply_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                  "bytes": spmv_bytes, "ms": apply_ms,
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
-    # the plain solve's FP64 flops delivered per second by the chosen form
+    # the method's flops delivered per second by the chosen form, against FP64
     fp64_equiv = {"tflops": f64_plain / (dom_ms * 1e-3) / 1e12,
                   "frac_of_fp64_peak": f64_plain / (dom_ms * 1e-3) / fp64_peak}
+    # kNN stencils (grid build + ring search): the output rows and the
+    # coordinates once (n x 4 + 8 d bytes per node, plus 8 d for the sorted copy
+    # and 12 for the cell keys, counts and permutation)
+    knn_bytes = ns.N * (DISK["interior"]["n"] * 4 + 8 * 2 * 2 + 12)
+    knn_roof = {"bound": "hbm", "kernel": "k_knn_grid<2> + grid build (whole kNN phase)",
+                "achieved": knn_bytes / (knn_ms * 1e-3) / 1e9, "unit": "GB/s", "peak": hbm,
+                "frac": (knn_bytes / (knn_ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                "bytes": knn_bytes, "ms": knn_ms, "nodes_per_s": ns.N / (knn_ms * 1e-3),
+                "note": "HBM reference of the survey; the ring search is bound by its integer and "
+                        "FP32 candidate tests, not by HBM",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": rk.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -639,7 +675,9 @@ def run_disk(args, rk):
             "fp64_plain": {"value": throughput(n_all, ms64, args.steps), "unit": "nodes/s",
                            "ms_per_step": ms64 / args.steps, "weights_ms": float(np.mean(w64)),
                            "dominant_ms": float(np.mean(d64)),
-                           "roofline_frac": f64_plain / (float(np.mean(d64)) * 1e-3) / fp64_peak},
+                           "roofline_frac": f64_plain / (float(np.mean(d64)) * 1e-3) / fp64_peak,
+                           "roofline_note": "bench.method_flops x interior rows / dominant_ms / "
+                                            "measured FP64 FMA peak"},
             "fp32_ir_wide64": {"value": throughput(n_all, msw, args.steps), "unit": "nodes/s",
                                "ms_per_step": msw / args.steps, "weights_ms": float(np.mean(ww)),
                                "dominant_ms": float(np.mean(dw)),
@@ -647,6 +685,7 @@ def run_disk(args, rk):
             "fp64_equivalent": fp64_equiv,
             "speedup_vs_fp64_plain": ms64 / ms, "weights_ms": float(np.mean(wts)),
             "fallback_fraction": fallback, "roofline": roof, "roofline_spmv": spmv_roof,
+            "roofline_knn": knn_roof,
             "roofline_combine": comb_roof,
             "peaks_measured": {"fp64_flops": fp64_peak, "fp32_flops": fp32_peak},
             "e2e": e2e, "clocks": clk, "gpu_launches": DISK_LAUNCHES_PER_STEP * args.steps}

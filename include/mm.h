@@ -39,6 +39,8 @@ extern "C" {
 #define MM_ENOMEM -2      /* workspace allocation failed                       */
 #define MM_ECUDA -3       /* a CUDA runtime call failed                        */
 #define MM_EUNSUPPORTED -4 /* a size or option outside what this build handles */
+#define MM_ENOCONV -5     /* an iterative solve stopped without converging     */
+#define MM_ESINGULAR -6   /* a zero pivot in a factorisation                   */
 
 /* ------------------------------------------------------- per-node statuses */
 #define MM_ST_OK 0
@@ -118,6 +120,10 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value);
 /* Message of the last failed call on this context ("" if none).  The string
  * is owned by the context and valid until its next call. */
 const char *mm_last_error(const mm_ctx *ctx);
+
+/* Bytes of device workspace the context holds now (0 until a call needed
+ * one; it only grows, and is freed by mm_ctx_destroy); -1 for NULL. */
+int64_t mm_ctx_workspace_bytes(const mm_ctx *ctx);
 
 /* -------------------------------------------------------------- stencils */
 /*
@@ -299,9 +305,14 @@ int mm_tile_table_load(mm_ctx *ctx, const char *path);
  *   Same arguments and results as mm_rbffd_weights(..., MM_FP32_IR, ...).
  *   At most 2^20 rows per call (row_end - row_begin); larger ranges fail
  *   with MM_EUNSUPPORTED before anything is enqueued.
- *   Calls no cudaMalloc, cudaFree or allocating library routine.  The first
- *   call on a device looks up the array's device address (cudaGetSymbolAddress)
- *   and caches it; make that first call before any stream capture.
+ *   Calls no cudaMalloc, cudaFree or allocating library routine, and never
+ *   touches the context workspace (mm_ctx_workspace_bytes stays as it was).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture.  Only a successful lookup is cached (a failed one is
+ *   retried by the next call).  The cached address is that of the device's
+ *   primary context: after cudaDeviceReset it is stale, so do not call this
+ *   entry point again in a process that reset the device.
  *   Every call shares the array, which keeps the last call's contents; the
  *   call clears the queue length on its stream first.  Calls whose GPU work
  *   overlaps (different streams, or different contexts on one device) race on

@@ -29,7 +29,7 @@ SCALE_FARTHEST, SCALE_NEAREST = 0, 1
 ROW_INTERNAL, ROW_DIRICHLET, ROW_NEUMANN = 0, 1, 2
 
 EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_option",
-           "mm_last_error", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
+           "mm_last_error", "mm_ctx_workspace_bytes", "mm_knn_stencils", "mm_rbffd_weights", "mm_apply_operator",
            "mm_diffuse", "mm_measure_fma_peak", "mm_rbffd_weights_ir_noalloc",
            "mm_rbffd_weights_batched", "mm_autotune_batched", "mm_tile_table_save",
            "mm_tile_table_load", "mm_mlp_create", "mm_mlp_destroy", "mm_mlp_num_params",
@@ -90,6 +90,7 @@ def load():
         lib.mm_ctx_set_option.argtypes = [vp, C.c_int, dbl]
         lib.mm_last_error.argtypes = [vp]
         lib.mm_last_error.restype = C.c_char_p
+        lib.mm_ctx_workspace_bytes.argtypes = [vp]
         lib.mm_knn_stencils.argtypes = [vp, C.c_int, i64, vp, C.c_int, C.POINTER(KnnRange),
                                         C.c_int, vp]
         lib.mm_rbffd_weights.argtypes = [vp, C.c_uint, C.c_int, C.c_int, C.c_int, i64, vp, vp,
@@ -131,9 +132,10 @@ def load():
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
         for name in EXPORTS:
             if name not in ("mm_ctx_destroy", "mm_last_error", "mm_mlp_destroy",
-                            "mm_mlp_num_params"):
+                            "mm_mlp_num_params", "mm_ctx_workspace_bytes"):
                 getattr(lib, name).restype = C.c_int
         lib.mm_mlp_num_params.restype = i64
+        lib.mm_ctx_workspace_bytes.restype = i64
         _lib = lib
         return lib
 
@@ -187,6 +189,10 @@ class Context:
     def set_stream(self, stream: torch.cuda.Stream):
         self.stream = stream
         self._check(self._lib.mm_ctx_set_stream(self._h, C.c_void_p(stream.cuda_stream)))
+
+    def workspace_bytes(self) -> int:
+        """Device workspace the context holds (mm_ctx_workspace_bytes)."""
+        return int(self._lib.mm_ctx_workspace_bytes(self._h))
 
     def set_option(self, key: int, value: float):
         self._check(self._lib.mm_ctx_set_option(self._h, key, float(value)))

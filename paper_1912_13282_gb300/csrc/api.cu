@@ -239,6 +239,8 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value) {
 
 const char *mm_last_error(const mm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+int64_t mm_ctx_workspace_bytes(const mm_ctx *ctx) { return ctx ? (int64_t)ctx->ws_bytes : -1; }
+
 int mm_knn_stencils(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
                     const mm_knn_range *ranges, int method, int32_t *d_status) {
     if (!ctx) return MM_EBADARG;

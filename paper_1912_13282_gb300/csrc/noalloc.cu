@@ -21,21 +21,27 @@ constexpr int64_t kNoAllocMaxRows = int64_t(1) << 20;   // rows per call
 static __device__ __align__(256) int g_fb_queue[1 + kNoAllocMaxRows];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-int *g_queue_addr[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
+std::mutex g_addr_mu;
+int *g_queue_addr[kMaxDevices];   // nullptr until a lookup on that device succeeded
 
 // Device address of g_fb_queue on `device` (which must be current).  In host
 // code the name g_fb_queue is only a host-side stand-in, so the address is
-// looked up once per device and cached.
+// looked up per device and cached.  Only a successful lookup is cached: a
+// failed one (e.g. attempted inside a stream capture) is retried by the next
+// call.  The cached address belongs to the device's primary context; after a
+// cudaDeviceReset it is stale, so a process that resets a device must not
+// call this entry point on it again.
 int queue_address(int device, int **out) {
     if (device < 0 || device >= kMaxDevices) return MM_EUNSUPPORTED;
-    std::call_once(g_once[device], [device] {
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (!g_queue_addr[device]) {
         void *p = nullptr;
-        g_setup_err[device] = cudaGetSymbolAddress(&p, g_fb_queue);
+        if (cudaGetSymbolAddress(&p, g_fb_queue) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MM_ECUDA;
+        }
         g_queue_addr[device] = (int *)p;
-    });
-    if (g_setup_err[device] != cudaSuccess || !g_queue_addr[device]) return MM_ECUDA;
+    }
     *out = g_queue_addr[device];
     return MM_OK;
 }
@@ -61,11 +67,9 @@ extern "C" int mm_rbffd_weights_ir_noalloc(mm_ctx *ctx, unsigned ops, int k, int
                        (long long)kNoAllocMaxRows, (long long)(row_end - row_begin));
     DeviceGuard g(ctx);
     int *queue = nullptr;
-    if (queue_address(ctx->device, &queue) != MM_OK) {
-        cudaGetLastError();
+    if (queue_address(ctx->device, &queue) != MM_OK)
         return mm_fail(ctx, MM_ECUDA, "cudaGetSymbolAddress of the fallback queue failed on device %d",
                        ctx->device);
-    }
     // the launch clears queue[0] on the stream before the solve kernel runs
     return weights_launch_scratch(ctx, job, MM_FP32_IR, queue, queue + 1);
 }

@@ -78,3 +78,22 @@ def monomial_residual(pts, normals, row_ptr, col, w, name, m, rows):
         res = np.abs(terms.sum(0) - lq) / np.maximum(1.0, np.abs(terms).sum(0))
         worst = max(worst, res.max())
     return worst
+
+
+def oracle_rows(oracle, pts, normals, rp, col, rows, k, m, ops, nthreads=8):
+    """Oracle weights for arbitrary rows of a CSR stencil pattern (the rows'
+    stencils renumbered locally, centres first): dict row -> [R, n] array."""
+    rows = np.asarray(rows)
+    st_list = [col[rp[i]:rp[i + 1]] for i in rows]
+    others = np.setdiff1d(np.unique(np.concatenate(st_list)), rows)
+    order = np.concatenate([rows, others])
+    remap = np.full(pts.shape[0], -1, dtype=np.int64)
+    remap[order] = np.arange(len(order))
+    Nl = None if normals is None else normals[order]
+    lcol = np.concatenate([remap[s] for s in st_list]).astype(np.int32)
+    lrp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum([len(s) for s in st_list], out=lrp[1:])
+    vals, status, _ = oracle.weights(pts[order], lrp, lcol, k, m, ops, normals=Nl,
+                                     rows=(0, len(rows)), nthreads=nthreads)
+    assert (status == 0).all()
+    return {int(i): vals[:, lrp[t]:lrp[t + 1]] for t, i in enumerate(rows)}

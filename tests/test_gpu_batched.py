@@ -111,6 +111,51 @@ def test_batched_equals_per_class(P, precision):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+def test_batched_matches_oracle_ball(P, oracle, precision):
+    """The persistent batched launch against the oracle directly (not only
+    through the per-class launches): the three ball classes (interior n = 35
+    r^3 deg 2, refined n = 60 deg 3, boundary n = 45 d/dn) in one call, 600
+    sampled rows per class, per-row error within 1e-10 (FP64; rows above that
+    only within 20 kappa_1 u64) or 1e-7 (FP32 + refinement), monomials
+    reproduced to 1e-12."""
+    from _helpers import monomial_residual, op_names, oracle_rows, rel_err_rows
+    ctx = P.Context(0)
+    prec = P.FP64 if precision == "fp64" else P.FP32_IR
+    spec = [("interior", 35, 3, 2, 1 | 2 | 4 | 8), ("refined", 60, 3, 3, 1 | 2 | 4 | 8),
+            ("boundary", 45, 3, 2, 16)]
+    g = Geometry(P, ctx, NS.ball(20000, seed=31), spec)
+    vals = g.new_vals()
+    ctx.rbffd_weights_batched(g.classes(P, vals), precision=prec)
+    torch.cuda.synchronize()
+    got = {b: v.cpu().numpy() for b, v in vals.items()}
+    st = g.status.cpu().numpy()
+    assert set(np.unique(st)) <= ({0} if precision == "fp64" else {0, P.binding.ST_FALLBACK})
+    col = g.col.cpu().numpy()
+    rng = np.random.default_rng(5)
+    u64 = np.finfo(np.float64).eps / 2
+    for cname, n, k, m, ops in spec:
+        b, e = g.ns.classes[cname]
+        rows = np.sort(rng.choice(np.arange(b, e), min(600, e - b), replace=False))
+        ref = oracle_rows(oracle, g.ns.pts, g.ns.normals, g.rp_h, col, rows, k, m, ops)
+        bits = [bit for bit in range(5) if ops & (1 << bit)]
+        for oi, (bit, nm) in enumerate(zip(bits, op_names(ops))):
+            w_ref = np.zeros_like(got[bit])
+            for i in rows:
+                w_ref[g.rp_h[i]:g.rp_h[i + 1]] = ref[int(i)][oi]
+            err = rel_err_rows(got[bit], w_ref, g.rp_h, rows)
+            if precision == "fp64":
+                for t in np.nonzero(err > 1e-10)[0]:
+                    i = rows[t]
+                    kap = oracle.kkt_cond1(g.ns.pts, col[g.rp_h[i]:g.rp_h[i + 1]], k, m)
+                    assert err[t] <= 20 * kap * u64, (cname, nm, int(i), err[t], kap)
+            else:
+                assert err.max() <= 1e-7, (cname, nm, err.max())
+            mono = monomial_residual(g.ns.pts, g.ns.normals, g.rp_h, col, got[bit], nm, m, rows[:300])
+            assert mono <= 1e-12, (cname, nm, mono)
+    ctx.close()
+
+
 def test_batched_weights_and_diffusion_in_one_graph(P):
     """Batched FP32+refined weights of several 2D/3D node sets and 10 explicit
     diffusion steps each, captured in one CUDA graph and replayed twice: the

@@ -70,9 +70,88 @@ def test_forward_and_gradients_match_oracle(P, ctx, oracle):
     lref, gref = oracle.mlp_grad(N_IN, H, L, N_OUT, params, x.astype(np.float32).astype(np.float64), t.astype(np.float32).astype(np.float64))
     assert abs(loss - lref) <= 2e-2 * lref
     gs, gr = split(g.astype(np.float64), N_IN, N_OUT), split(gref, N_IN, N_OUT)
-    for name, _ in blocks(N_IN, N_OUT):
-        e = np.linalg.norm(gs[name] - gr[name]) / max(np.linalg.norm(gr[name]), 1e-30)
-        assert e <= 5e-2, (name, e)
+    errs = {name: float(np.linalg.norm(gs[name] - gr[name]) / max(np.linalg.norm(gr[name]), 1e-30))
+            for name, _ in blocks(N_IN, N_OUT)}
+    # BF16 operands (u = 2^-8) in the forward and backward GEMMs, FP32 sums:
+    # about 1e-2 relative in norm per parameter block
+    assert max(errs.values()) <= 1e-2, errs
+    net.close()
+
+
+def _bf16_forward_sigma(params, x, mean_std=None):
+    """Per-element scale of |y_bf16 - y| for the network evaluated with BF16
+    weights and activations and FP32 accumulation, from the layer widths, by
+    probabilistic rounding-error analysis (Higham & Mary, SIAM J. Sci.
+    Comput. 2019: independent rounding errors of unit roundoff u add up like
+    sqrt(n) u instead of n u).  Each rounding is modelled as a relative error
+    uniform in [-u, u] (variance u^2/3), u = 2^-8 for BF16: the input, every
+    weight and every stored activation; the hardware tanh of GELU adds an
+    absolute error below 2^-11 |z|.  Variances propagate through layer l as
+        V_l = W_l^2 v_{l-1} + (u^2/3) W_l^2 h_{l-1}^2,
+        v_l = 1.13^2 V_l + (u^2/3) h_l^2 + (2^-22/3) z_l^2,  v_0 = (u^2/3) x^2,
+    sums over the layer's input width, 1.13 the largest slope of GELU.  The
+    FP64 activations h_l, z_l are recomputed here only to evaluate the scale;
+    returns sqrt(V_4) times the output scaling."""
+    u2 = 2.0 ** -16 / 3
+    sp = split(params, N_IN, N_OUT)
+    c = np.sqrt(2 / np.pi)
+    h = x
+    v = u2 * x * x
+    for l in range(1, 5):
+        W, b = sp[f"W{l}"].reshape(-1, h.shape[1]), sp[f"b{l}"]
+        W2 = W * W
+        z = h @ W.T + b
+        V = v @ W2.T + u2 * ((h * h) @ W2.T)
+        if l == 4:
+            out = np.sqrt(V)
+            break
+        h = 0.5 * z * (1 + np.tanh(c * (z + 0.044715 * z ** 3)))
+        v = 1.13 ** 2 * V + u2 * h * h + 2.0 ** -22 / 3 * z * z
+    if mean_std is not None:
+        out = out * np.abs(mean_std[1])[None, :]
+    return out
+
+
+@pytest.mark.parametrize("B", [1, 127, 129, 65536 + 129])
+def test_fused_inference_matches_oracle_elementwise(P, ctx, oracle, B):
+    """The fused tensor-core forward (tcgen05) against the FP64 oracle forward
+    of the same FP32 parameters, element by element: every output within
+    lambda = 4 of the rounding-error scale of _bf16_forward_sigma (a sum of
+    independent roundings exceeds 4 sigma with probability below 2 exp(-8)
+    per element; the scale's GELU slope 1.13 already overstates the typical
+    one, and a BF16 emulation of the network stays below 0.7 sigma), for a
+    single row, a partial tile, one row past a tile and more tiles than SMs
+    with a ragged tail.  Also: the model is not loose (the 99th percentile
+    of |error| / sigma is at least 0.1)."""
+    net = P.MLP(ctx, N_IN, N_OUT, seed=17)
+    rng = np.random.default_rng(B)
+    p = net.get_params()
+    p += rng.normal(scale=0.02, size=p.shape).astype(np.float32)   # nonzero biases too
+    net.set_params(p)
+    mean, std = rng.normal(size=N_OUT), rng.uniform(0.5, 2.0, size=N_OUT)
+    net.set_output_scaling(mean, std)
+    mean, std = mean.astype(np.float32).astype(np.float64), std.astype(np.float32).astype(np.float64)
+    x = rng.uniform(-1, 1, size=(B, N_IN)).astype(np.float32)
+    y = torch.full((B, N_OUT), float("nan"), device="cuda")
+    net.forward(torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.float64)
+    params = net.get_params().astype(np.float64)
+    # the oracle in chunks (its forward holds B x 256 activations per layer)
+    ref = np.empty_like(got)
+    bound = np.empty_like(got)
+    for a in range(0, B, 8192):
+        xb = x[a:a + 8192].astype(np.float64)
+        yo, _ = oracle.mlp_forward(N_IN, H, L, N_OUT, params, xb)
+        ref[a:a + 8192] = yo * std + mean
+        bound[a:a + 8192] = _bf16_forward_sigma(params, xb, (mean, std))
+    assert np.isfinite(got).all()
+    ratio = np.abs(got - ref) / bound
+    worst = np.unravel_index(np.argmax(ratio), ratio.shape)
+    assert ratio.max() <= 4.0, (float(ratio.max()), worst, float(got[worst]), float(ref[worst]),
+                                float(bound[worst]))
+    if B >= 127:
+        assert np.quantile(ratio, 0.99) >= 0.1, float(np.quantile(ratio, 0.99))
     net.close()
 
 
@@ -217,5 +296,19 @@ def _surrogate_path_checks(P, ctx, oracle, net, S):
         proj = oracle.project_lap(pts_h, stn, k, m, pred_h[i])
         got = w[rp_h[i]:rp_h[i + 1]] * s_h[i] ** 2
         assert np.abs(got - proj).max() <= 1e-9 * np.abs(proj).max()
-        rho_o = oracle.phi_residual_lap(pts_h, stn, k, m, proj)
-        assert abs(rho_o - r[i]) <= 1e-3, (rho_o, r[i])
+    # rho against the oracle's, relatively, on accepted and rejected rows; the
+    # accept/reject decision equals the oracle's wherever rho is clear of tau
+    # by more than that tolerance (the GPU check runs in FP32: about u32 times
+    # sum |A_ij w_j| ~ 1e-5 of ||l_phi|| absolute)
+    sample = np.concatenate([np.nonzero(acc)[0][:200], np.nonzero(~acc)[0][:200]])
+    rho_o = np.empty(len(sample))
+    for t, i in enumerate(sample):
+        stn = col_h[rp_h[i]:rp_h[i + 1]]
+        proj = oracle.project_lap(pts_h, stn, k, m, pred_h[i])
+        rho_o[t] = oracle.phi_residual_lap(pts_h, stn, k, m, proj)
+    rho_g = r[sample].astype(np.float64)
+    tol = 0.02 * rho_o + 2e-5
+    assert (np.abs(rho_g - rho_o) <= tol).all(), float((np.abs(rho_g - rho_o) / (rho_o + 1e-30)).max())
+    clear = np.abs(rho_o - tau) > 0.02 * tau + 2e-5
+    assert clear.sum() >= 0.8 * len(sample)
+    assert np.array_equal(acc[sample][clear], rho_o[clear] <= tau)

@@ -484,6 +484,61 @@ def test_projection(oracle):
         assert oracle.phi_residual_lap(ns.pts, st, 5, 4, w) > 1e-4
 
 
+def test_phi_residual_hand_worked(oracle):
+    """rho on a stencil worked out by hand.  Four nodes at the corners of a
+    square of side h, centre first; k = 3, m = 1 (l = 3, so n = l + 1): the
+    residual r = l_phi - A w minus its least-squares fit by Q is r's component
+    along the single null vector v = (1, -1, -1, 1) of Q^T, so
+    ||r - Q lambda||_inf = |v.r| / 4.  With s = sqrt(2) h and a = 1/sqrt(2):
+    xi = (0,0), (a,0), (0,a), (a,a); l_phi,j = k (k + d - 2) r_j^(k-2) = 9 r_j
+    = (0, 9a, 9a, 9), so ||l_phi||_inf = 9; column j of A holds
+    ||xi_i - xi_j||^3 (here h = 0.1)."""
+    pts = np.array([[0.3, 0.2], [0.4, 0.2], [0.3, 0.3], [0.4, 0.3]])
+    st = np.arange(4, dtype=np.int32)
+    a = 1 / math.sqrt(2)
+    vl = 0 - 9 * a - 9 * a + 9                         # v . l_phi
+    cases = {
+        "zero": (np.zeros(4), vl),
+        # A e_0 = (0, a^3, a^3, 1): v . A e_0 = 1 - 2 a^3
+        "centre": (np.array([1.0, 0, 0, 0]), vl - (1 - 2 * a ** 3)),
+        # A e_1 = (a^3, 0, 1, a^3): v . A e_1 = 2 a^3 - 1
+        "node1": (np.array([0, 1.0, 0, 0]), vl - (2 * a ** 3 - 1)),
+        # A e_3 = (1, a^3, a^3, 0): v . A (2 e_0 - e_3) = 2 (1 - 2 a^3) - (1 - 2 a^3)
+        "mixed": (np.array([2.0, 0, 0, -1.0]), vl - 2 * (1 - 2 * a ** 3) + (1 - 2 * a ** 3)),
+    }
+    for name, (w, vr) in cases.items():
+        ref = abs(vr) / 4 / 9
+        got = oracle.phi_residual_lap(pts * 1.0, st, 3, 1, w)
+        assert abs(got - ref) <= 1e-14, (name, got, ref)
+    # the scale of the node set does not matter (w is in scaled units)
+    got = oracle.phi_residual_lap(pts * 7.0 + 1.0, st, 3, 1, np.zeros(4))
+    assert abs(got - (math.sqrt(2) - 1) / 4) <= 1e-14
+
+
+def test_phi_residual_equals_orthogonal_complement(oracle):
+    """On disk stencils (n = 25, k = 5, m = 4) rho equals the sup norm of the
+    part of l_phi - A w orthogonal to range(Q), taken with an SVD projector
+    (numpy), over ||l_phi||_inf; for exact weights it is ~0, and it grows
+    linearly when w moves off them inside null(Q^T)."""
+    ns = NS.disk_holes(8000, seed=5)
+    _, stencils = random_stencils(ns, 25, 6, 4, oracle)
+    rng = np.random.default_rng(11)
+    n = 25
+    for st in stencils:
+        K, B, xi, s = oracle.kkt(ns.pts, st, 5, 4, 1)
+        A, Q, lphi = K[:n, :n], K[:n, n:], B[:n, 0]
+        U, sv, _ = np.linalg.svd(Q, full_matrices=True)
+        Z = U[:, Q.shape[1]:]                           # basis of null(Q^T)
+        exact = np.linalg.solve(K, B)[:n, 0]
+        for t in (1e-3, 1e-2, 1e-1):
+            d = Z @ rng.normal(size=Z.shape[1])
+            w = exact + t * d / np.abs(d).max() * np.abs(exact).max()
+            r = lphi - A @ w
+            ref = np.abs(Z @ (Z.T @ r)).max() / np.abs(lphi).max()
+            got = oracle.phi_residual_lap(ns.pts, st, 5, 4, w)
+            assert abs(got - ref) <= 1e-9 * max(ref, 1e-6), (t, got, ref)
+
+
 # ------------------------------------------------------------------------ MLP
 def test_mlp_gradient_finite_differences(oracle):
     n_in, H, L, n_out, B = 5, 7, 3, 4, 6
