@@ -383,6 +383,75 @@ int mm_combine_operators(mm_ctx *ctx, const mm_csr_pattern *stencils, int64_t ro
                          int nterms, const double *const *d_terms, const double *const *d_coef,
                          double *d_out);
 
+/* ----------------------------------------------------------- implicit solve */
+/*
+ * The implicit discretisation of Section 2.3.2: every node's equation becomes
+ * one sparse row -- interior nodes the weights of the PDE's operator (e.g.
+ * the Laplacian of the Poisson problem of Section 5), Dirichlet nodes the
+ * identity, Neumann nodes their d/dn weights -- and M u = r is solved with
+ * BiCGSTAB preconditioned by an incomplete LU factorisation (the paper's
+ * benchmark uses ILUT; this library uses ILU(0), the incomplete LU on the
+ * pattern of M, no dropping and no fill-in).
+ *
+ * Matrices of these calls are square CSR (nrows == number of unknowns, at
+ * most 64 entries per row, column indices in [0, nrows)) on the device.
+ */
+
+/*
+ * Assembles the implicit matrix from stencil rows: row i's entries sorted by
+ * column into d_col_out / d_vals_out (same row pointers as `stencils`, which
+ * must list node i in row i); rows with d_kind[i] == MM_ROW_DIRICHLET become
+ * the identity row on the same pattern (1 on the diagonal, explicit zeros
+ * elsewhere), every other row keeps the values of d_vals (interior: the
+ * operator's weights, MM_ROW_NEUMANN: the d/dn weights).  d_kind NULL: no
+ * Dirichlet rows.  The right-hand side is the caller's (f, the Dirichlet
+ * values, g_n).  Synchronises (to report bad rows).
+ * Errors: MM_EBADARG (a row without its own index, a repeated or out-of-range
+ * column), MM_EUNSUPPORTED (a row of more than 64 entries), MM_ECUDA.
+ */
+int mm_implicit_assemble(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
+                         const uint8_t *d_kind, int32_t *d_col_out, double *d_vals_out);
+
+/*
+ * ILU(0) factors of the sorted matrix A (rows with increasing columns and a
+ * diagonal entry): d_factors [nnz] receives L (unit diagonal implied, strictly
+ * lower entries) and U (the rest) on A's pattern, so that (L U)_ij = A_ij for
+ * every (i, j) of the pattern; d_diag [nrows] the position of each diagonal
+ * entry.  Rows are eliminated in the plain row-by-row order with IEEE
+ * roundings and no fused multiply-add, so the factors equal those of the
+ * sequential algorithm bit for bit.  d_factors may equal d_vals (in place).
+ * Synchronises.  Errors: MM_EBADARG (unsorted row, missing diagonal),
+ * MM_ESINGULAR (a zero pivot), MM_EUNSUPPORTED (a row longer than 64),
+ * MM_ECUDA (including a dependency wait that timed out).
+ */
+int mm_ilu0(mm_ctx *ctx, const mm_csr_pattern *A, const double *d_vals, double *d_factors,
+            int64_t *d_diag);
+
+/*
+ * x = (L U)^-1 b with the factors of mm_ilu0 on the same pattern: forward
+ * then back substitution, each row waiting only for the unknowns it needs
+ * (no level sets).  d_b and d_x are [nrows], distinct.  Synchronises.
+ * Errors: MM_EBADARG, MM_ECUDA.
+ */
+int mm_ilu0_solve(mm_ctx *ctx, const mm_csr_pattern *A, const double *d_factors,
+                  const int64_t *d_diag, const double *d_b, double *d_x);
+
+/*
+ * BiCGSTAB (van der Vorst's algorithm) for A x = b, preconditioned by the
+ * ILU(0) factors d_factors / d_diag of A (NULL: no preconditioner), starting
+ * from the d_x given; stops when the recursively updated residual satisfies
+ * ||r||_2 <= tol ||b||_2, on a breakdown (rho or omega or r^.v equal to 0) or
+ * after maxit iterations.  All scalars stay on the GPU; the host looks at
+ * them every 16 iterations (later iterations of that batch do nothing).
+ * *iters and *relres (either may be NULL) receive the iterations taken and
+ * the final relative residual.  Synchronises.
+ * Errors: MM_ENOCONV (breakdown or iteration limit; d_x holds the last
+ * iterate), MM_EBADARG, MM_ENOMEM, MM_ECUDA.
+ */
+int mm_bicgstab(mm_ctx *ctx, const mm_csr_pattern *A, const double *d_vals,
+                const double *d_factors, const int64_t *d_diag, const double *d_b, double *d_x,
+                double tol, int maxit, int *iters, double *relres);
+
 /* ------------------------------------------------- learned surrogate (MLP) */
 /*
  * A GELU multilayer perceptron n_in -> 256 -> 256 -> 256 -> n_out that maps

@@ -15,7 +15,7 @@ import torch
 
 from . import _build
 
-MM_OK, MM_EBADARG, MM_ENOMEM, MM_ECUDA, MM_EUNSUPPORTED = 0, -1, -2, -3, -4
+MM_OK, MM_EBADARG, MM_ENOMEM, MM_ECUDA, MM_EUNSUPPORTED, MM_ENOCONV, MM_ESINGULAR = 0, -1, -2, -3, -4, -5, -6
 ST_OK, ST_SINGULAR, ST_NONCONVERGED, ST_FALLBACK, ST_BADARG, ST_DUPLICATE, ST_ACCEPTED = range(7)
 LAP, DX, DY, DZ, DN = 1, 2, 4, 8, 16
 DXX, DXY, DYY, DXZ, DYZ, DZZ = 32, 64, 128, 256, 512, 1024
@@ -36,7 +36,7 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_output_scaling",
            "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
            "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights", "mm_diffuse_bc",
-           "mm_combine_operators"]
+           "mm_combine_operators", "mm_implicit_assemble", "mm_ilu0", "mm_ilu0_solve", "mm_bicgstab"]
 
 
 class KnnRange(C.Structure):
@@ -129,6 +129,11 @@ def load():
         lib.mm_diffuse_bc.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, dbl, C.c_int, vp, vp]
         lib.mm_combine_operators.argtypes = [vp, C.POINTER(CsrPattern), i64, i64, C.c_int, C.POINTER(vp),
                                              C.POINTER(vp), vp]
+        lib.mm_implicit_assemble.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, vp]
+        lib.mm_ilu0.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp]
+        lib.mm_ilu0_solve.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, vp]
+        lib.mm_bicgstab.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, vp, vp, dbl, C.c_int,
+                                    C.POINTER(C.c_int), C.POINTER(dbl)]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
         for name in EXPORTS:
             if name not in ("mm_ctx_destroy", "mm_last_error", "mm_mlp_destroy",
@@ -406,6 +411,56 @@ class Context:
             *[None if a is None else a.data_ptr() for a in coefs])
         self._check(self._lib.mm_combine_operators(self._h, C.byref(pat), row_begin, row_end, len(terms),
                                                    tp, cp, _ptr(out)))
+
+    # ------------------------------------------------------- implicit solve
+    def implicit_assemble(self, row_ptr, col, vals, kind, col_out, vals_out):
+        """mm_implicit_assemble: rows sorted by column, Dirichlet rows (kind
+        == ROW_DIRICHLET, uint8 [nrows] or None) replaced by the identity."""
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        _dev(vals, "vals", torch.float64)
+        _dev(col_out, "col_out", torch.int32)
+        _dev(vals_out, "vals_out", torch.float64)
+        if kind is not None:
+            _dev(kind, "kind", torch.uint8)
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        self._check(self._lib.mm_implicit_assemble(self._h, C.byref(pat), _ptr(vals), _ptr(kind),
+                                                   _ptr(col_out), _ptr(vals_out)))
+
+    def ilu0(self, row_ptr, col, vals, factors, diag):
+        """mm_ilu0 on a sorted CSR matrix; factors float64 [nnz] (may be vals),
+        diag int64 [nrows]."""
+        _dev(row_ptr, "row_ptr", torch.int64)
+        _dev(col, "col", torch.int32)
+        _dev(vals, "vals", torch.float64)
+        _dev(factors, "factors", torch.float64)
+        _dev(diag, "diag", torch.int64)
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        self._check(self._lib.mm_ilu0(self._h, C.byref(pat), _ptr(vals), _ptr(factors), _ptr(diag)))
+
+    def ilu0_solve(self, row_ptr, col, factors, diag, b, x):
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        for t, nm, dt in ((row_ptr, "row_ptr", torch.int64), (col, "col", torch.int32),
+                          (factors, "factors", torch.float64), (diag, "diag", torch.int64),
+                          (b, "b", torch.float64), (x, "x", torch.float64)):
+            _dev(t, nm, dt)
+        self._check(self._lib.mm_ilu0_solve(self._h, C.byref(pat), _ptr(factors), _ptr(diag), _ptr(b),
+                                            _ptr(x)))
+
+    def bicgstab(self, row_ptr, col, vals, b, x, factors=None, diag=None, tol=1e-10, maxit=1000,
+                 check=True):
+        """mm_bicgstab; returns (return code, iterations, relative residual).
+        With check=True a code other than MM_OK or MM_ENOCONV raises."""
+        pat = CsrPattern(row_ptr.numel() - 1, col.numel(), row_ptr.data_ptr(), col.data_ptr())
+        for t, nm, dt in ((row_ptr, "row_ptr", torch.int64), (col, "col", torch.int32),
+                          (vals, "vals", torch.float64), (b, "b", torch.float64), (x, "x", torch.float64)):
+            _dev(t, nm, dt)
+        it, res = C.c_int(0), C.c_double(0.0)
+        rc = self._lib.mm_bicgstab(self._h, C.byref(pat), _ptr(vals), _ptr(factors), _ptr(diag), _ptr(b),
+                                   _ptr(x), float(tol), int(maxit), C.byref(it), C.byref(res))
+        if check and rc not in (MM_OK, MM_ENOCONV):
+            self._check(rc)
+        return rc, it.value, res.value
 
     def measure_fma_peak(self, which: int) -> float:
         out = C.c_double()
