@@ -177,6 +177,13 @@ def weight_case(name):
     elif name == "disk":
         ns = NS.disk_holes(20000, seed=5)
         spec = [("interior", 25, 5, 4, 1 | 2 | 4), ("boundary", 30, 5, 4, 16)]
+    elif name.startswith("disk_r"):
+        # every operator count R = 1..5 of the solvers (each R is its own
+        # kernel instance): 25-node interior rows (M = 40, register inverse)
+        # and 30-node boundary rows (M = 45)
+        ops = {"disk_r1": 1, "disk_r2": 2 | 4, "disk_r4": 1 | 2 | 4 | 32, "disk_r5": 1 | 2 | 4 | 32 | 128}[name]
+        ns = NS.disk_holes(20000, seed=8)
+        spec = [("interior", 25, 5, 4, ops), ("boundary", 30, 5, 4, ops if name != "disk_r1" else 16)]
     else:
         ns = NS.ball(15000, seed=6)
         spec = [("interior", 35, 3, 2, 1 | 2 | 4 | 8), ("refined", 60, 3, 3, 1 | 2 | 4 | 8),
@@ -204,7 +211,8 @@ def weight_inputs(P, ctx):
     return get
 
 
-@pytest.mark.parametrize("name", ["square", "disk", "ball", "square_d2", "disk_d2", "ball_d2"])
+@pytest.mark.parametrize("name", ["square", "disk", "ball", "square_d2", "disk_d2", "ball_d2", "disk_r1",
+                                  "disk_r2", "disk_r4", "disk_r5"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_ir", "fp32_ir_wide64"])
 def test_weights_match_oracle(P, ctx, oracle, weight_inputs, name, precision):
     """fp32_ir refines with double-FP32 residuals (the default), fp32_ir_wide64
