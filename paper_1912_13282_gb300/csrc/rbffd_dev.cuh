@@ -169,7 +169,9 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
     const int lane = threadIdx.x & 31;
     const int l = P.l, M = qoff + l, k = P.k;
     const int di = DIM - 2;
-    double amax = 0.0;
+    // max |K| kept as the largest bit pattern of the (non-negative) |values|:
+    // integer compares instead of FP64 ones
+    unsigned long long amax_bits = 0ull;
     // A: unordered pairs (r, (r + d) mod n), d = 1 .. n/2, each once
     for (int d = 1; d <= n / 2; ++d) {
         int cnt = (2 * d == n) ? n / 2 : n;
@@ -185,7 +187,7 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
             double v = phs(r2, k);
             K[r * pitch + c] = v;
             K[c * pitch + r] = v;
-            amax = fmax(amax, v);
+            amax_bits = max(amax_bits, (unsigned long long)__double_as_longlong(v));
         }
     }
     for (int r = lane; r < n; r += 32) K[r * pitch + r] = 0.0;
@@ -207,10 +209,9 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
             double v = Kr[c_mono.parent[di][b]] * xi[r * DIM + c_mono.var[di][b]];
             Kr[b] = v;
             K[(qoff + b) * pitch + r] = v;
-            amax = fmax(amax, fabs(v));
+            amax_bits = max(amax_bits, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
         }
     }
-    amax = fmax(amax, 1.0);
     for (int e = lane; e < l * l; e += 32) K[(qoff + e / l) * pitch + qoff + e % l] = 0.0;
     // right-hand sides in columns M .. M+R-1
     for (int j = lane; j < n; j += 32) {
@@ -260,7 +261,9 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
         }
     }
     __syncwarp();
-    return warp_max(amax);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(kFull, amax_bits, o));
+    return fmax(__longlong_as_double((long long)amax_bits), 1.0);
 }
 
 // Unscaled store of the first n rows of columns M..M+R-1 of X (pitch xp).
@@ -277,6 +280,30 @@ __device__ void store_weights(const WParams &P, int64_t rb, int n, double s, con
 }
 
 // ------------------------------------------------------------ FP64 solver
+// Pivot key of an FP64 value in row r (< 128): the high word of |v| (sign,
+// exponent, 20 mantissa bits) with its 7 lowest bits replaced by 127 - r, so
+// the largest key is the largest |v| to 13 mantissa bits, the lowest row on
+// ties.  Keys compare as integers: the search runs on the integer pipe and
+// one redux.sync, not on the FP64 pipe (1/74 of the FP32 rate on GB300).
+__device__ __forceinline__ unsigned pivot_key64(double v, int r) {
+    const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7FFFFFFFu;
+    return (hi & 0xFFFFFF80u) | (unsigned)(127 - r);
+}
+
+// 1/d by Newton-Raphson iteration for the reciprocal, y <- y + y (1 - d y),
+// from the FP32 reciprocal of d: each step squares the relative error
+// (2^-23 -> 2^-46 -> below FP64 rounding), i.e. 4 FP64 FMAs instead of a
+// full IEEE division.  Pivots outside the FP32 normal range take the division.
+__device__ __forceinline__ double recip_nr(double d) {
+    const double a = fabs(d);
+    if (!(a > 1e-30 && a < 1e30)) return 1.0 / d;
+    double y = (double)__frcp_rn((float)d);
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    return fma(y, e, y);
+}
+
 // Gaussian elimination with row partial pivoting on [K | B] (M rows, M+R
 // columns), then back substitution; solution overwrites columns M..M+R-1.
 // Returns false if a pivot is not larger than M * u * amax.
@@ -286,14 +313,11 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
     const double tiny = (double)M * (DBL_EPSILON * 0.5) * amax;
     const int W_all = M + R;
     for (int kk = 0; kk < M; ++kk) {
-        double best = -1.0;
-        int prow = M;
-        for (int r = kk + lane; r < M; r += 32) {
-            double v = fabs(K[r * pitch + kk]);
-            if (v > best) { best = v; prow = r; }
-        }
-        warp_argmax(best, prow);
-        if (!(best > tiny)) return false;
+        unsigned key = 0;
+        for (int r = kk + lane; r < M; r += 32) key = max(key, pivot_key64(K[r * pitch + kk], r));
+        const int prow = 127 - (int)(__reduce_max_sync(kFull, key) & 0x7Fu);
+        const double piv = K[prow * pitch + kk];
+        if (!(fabs(piv) > tiny)) return false;
         if (prow != kk) {
             for (int c = kk + lane; c < W_all; c += 32) {
                 double t = K[kk * pitch + c];
@@ -302,7 +326,7 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
             }
             __syncwarp();
         }
-        double ip = 1.0 / K[kk * pitch + kk];
+        const double ip = recip_nr(piv);
         if (lane == 0) invp[kk] = ip;
         for (int r = kk + 1 + lane; r < M; r += 32) mul[r] = K[r * pitch + kk] * ip;
         __syncwarp();

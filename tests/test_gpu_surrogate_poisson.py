@@ -14,7 +14,8 @@ refinement solve.  Measured trade-off, asserted here:
     that is no longer equal to FP64's (the accepted weights carry the
     network's ~1% error).
 So at equal Poisson error the surrogate gains nothing over the FP32 +
-refinement solve with this network; its gain is speed at a larger error.
+refinement solve with this network; its gain is speed at a larger error, and
+only when the network is trained well enough to accept most stencils.
 """
 import numpy as np
 import pytest
@@ -32,9 +33,12 @@ def setup():
     import paper_1912_13282_gb300 as P
     from paper_1912_13282_gb300 import surrogate as S
     ctx = P.Context(0)
-    data = S.make_dataset(ctx, 1 << 19, seed=1)
+    # the benchmark's network: 2^20 patch stencils, 120 epochs (a network
+    # trained on 2^19 stencils for 80 epochs accepted fewer stencils and was
+    # no faster than the solve even at tau = 1e-3)
+    data = S.make_dataset(ctx, 1 << 20, seed=1)
     net = P.MLP(ctx, 50, 25, seed=0)
-    S.train(net, data["x"], data["t"], epochs=80, batch=4096, lr=3e-3, lr_final=1e-4)
+    S.train(net, data["x"], data["t"], epochs=120, batch=4096, lr=3e-3, lr_final=1e-4)
     del data
     yield P, ctx, net
     net.close()
