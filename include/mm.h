@@ -530,6 +530,45 @@ int mm_rbffd_weights_surrogate(mm_ctx *ctx, mm_mlp *net, int k, int m, int dim, 
                                int fallback_precision, double *d_lap_vals, int32_t *d_status,
                                float *d_rho);
 
+/* ------------------------------------------------------- range partition */
+/*
+ * Splitting one node set over several GPUs.  The weights of every node come
+ * from its own stencil (Section 2.2), so the node set splits into contiguous
+ * ranges of a space-filling order, one per GPU; each GPU also holds the halo
+ * of its range (the nodes of other ranges within a radius of its own), forms
+ * its nodes' stencils and operator rows from range + halo, and an explicit
+ * step (Section 2.3.1) needs only the halo's new values from the other GPUs.
+ * The paper names distributed execution as future work (Section 6).  Both
+ * calls are host-only (no context, no GPU) and take host arrays.
+ */
+
+/*
+ * Morton (Z-order) permutation of the N nodes h_pts [N x dim] (coordinates
+ * quantised to a common grid over the bounding box, 31 bits per axis in 2D,
+ * 21 in 3D; equal codes in index order): h_perm [N] receives the original
+ * index of the k-th node in that order, h_starts [nparts + 1] the balanced
+ * range boundaries (h_starts[p] = floor(N p / nparts)); range p is
+ * h_perm[h_starts[p] .. h_starts[p+1]-1].
+ * Errors: MM_EBADARG (dim not 2/3, non-finite points, nparts outside [1, N]).
+ */
+int mm_partition_morton(int dim, int64_t N, const double *h_pts, int nparts, int64_t *h_perm,
+                        int64_t *h_starts);
+
+/*
+ * Halo of the range h_perm[begin .. end-1]: every node outside it whose
+ * distance to some node of the range is <= radius, in increasing index order,
+ * into h_halo [capacity]; *nhalo receives the count (also when it exceeds
+ * capacity, which returns MM_EUNSUPPORTED with the first `capacity` written).
+ * With range + halo as the candidates, a range node's n-node stencil is
+ * exactly its stencil in the whole set (mm_knn_stencils' ranking) whenever
+ * its n-th closest candidate lies within `radius` of it: every node closer
+ * than that is within the radius, hence among the candidates.
+ * Errors: MM_EBADARG (bad points, range, radius, or h_perm not a permutation
+ * on the range), MM_EUNSUPPORTED (capacity too small).
+ */
+int mm_partition_halo(int dim, int64_t N, const double *h_pts, const int64_t *h_perm, int64_t begin,
+                      int64_t end, double radius, int64_t *h_halo, int64_t capacity, int64_t *nhalo);
+
 /* ------------------------------------------------------------- measurement */
 /*
  * Measured arithmetic peak of this GPU for the pipe `which` (0 = FP64 FMA,

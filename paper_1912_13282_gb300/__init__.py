@@ -9,4 +9,5 @@ include/mm.h); ``binding`` is a thin ctypes layer over it.
 from . import _build  # noqa: F401
 from .binding import (DN, DX, DXX, DXY, DXZ, DY, DYY, DYZ, DZ, DZZ, FP32_IR, FP64, KNN_AUTO,  # noqa: F401
                       KNN_BRUTE, KNN_GRID, LAP, MLP, SCALE_FARTHEST, SCALE_NEAREST, Context, MMError,
-                      load, rbffd_weights_surrogate, stencil_features)
+                      load, partition_halo, partition_morton, rbffd_weights_surrogate,
+                      stencil_features)

@@ -36,7 +36,8 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_output_scaling",
            "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
            "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights", "mm_diffuse_bc",
-           "mm_combine_operators", "mm_implicit_assemble", "mm_ilu0", "mm_ilu0_solve", "mm_bicgstab"]
+           "mm_combine_operators", "mm_implicit_assemble", "mm_ilu0", "mm_ilu0_solve", "mm_bicgstab",
+           "mm_partition_morton", "mm_partition_halo"]
 
 
 class KnnRange(C.Structure):
@@ -134,6 +135,8 @@ def load():
         lib.mm_ilu0_solve.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, vp]
         lib.mm_bicgstab.argtypes = [vp, C.POINTER(CsrPattern), vp, vp, vp, vp, vp, dbl, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(dbl)]
+        lib.mm_partition_morton.argtypes = [C.c_int, i64, vp, C.c_int, vp, vp]
+        lib.mm_partition_halo.argtypes = [C.c_int, i64, vp, vp, i64, i64, dbl, vp, i64, C.POINTER(i64)]
         lib.mm_measure_fma_peak.argtypes = [vp, C.c_int, C.POINTER(dbl)]
         for name in EXPORTS:
             if name not in ("mm_ctx_destroy", "mm_last_error", "mm_mlp_destroy",
@@ -466,6 +469,42 @@ class Context:
         out = C.c_double()
         self._check(self._lib.mm_measure_fma_peak(self._h, which, C.byref(out)))
         return out.value
+
+
+def partition_morton(pts, nparts: int):
+    """mm_partition_morton on host points (numpy [N, dim]): (perm, starts)."""
+    import numpy as np
+    lib = load()
+    p = np.ascontiguousarray(pts, dtype=np.float64)
+    N, dim = p.shape
+    perm = np.empty(N, dtype=np.int64)
+    starts = np.empty(nparts + 1, dtype=np.int64)
+    rc = lib.mm_partition_morton(dim, N, p.ctypes.data_as(C.c_void_p), nparts, perm.ctypes.data_as(C.c_void_p),
+                                 starts.ctypes.data_as(C.c_void_p))
+    if rc != MM_OK:
+        raise MMError(f"mm_partition_morton failed ({rc})")
+    return perm, starts
+
+
+def partition_halo(pts, perm, begin: int, end: int, radius: float):
+    """mm_partition_halo: indices of the nodes outside perm[begin:end] within
+    `radius` of one of its nodes (increasing)."""
+    import numpy as np
+    lib = load()
+    p = np.ascontiguousarray(pts, dtype=np.float64)
+    pm = np.ascontiguousarray(perm, dtype=np.int64)
+    N, dim = p.shape
+    cap = max(1024, 2 * (end - begin))
+    while True:
+        halo = np.empty(cap, dtype=np.int64)
+        cnt = C.c_int64(0)
+        rc = lib.mm_partition_halo(dim, N, p.ctypes.data_as(C.c_void_p), pm.ctypes.data_as(C.c_void_p), begin, end,
+                                   float(radius), halo.ctypes.data_as(C.c_void_p), cap, C.byref(cnt))
+        if rc == MM_OK:
+            return halo[:cnt.value].copy()
+        if rc != MM_EUNSUPPORTED:
+            raise MMError(f"mm_partition_halo failed ({rc})")
+        cap = int(cnt.value)
 
 
 class MLP:
