@@ -1103,11 +1103,21 @@ def run_surrogate(args, rk):
                               "fallback_max": float(err[~acc].max()) if (~acc).any() else None},
             "training": {"samples": ntrain, "steps": int(len(losses)), "seconds": t_train,
                          "data_seconds": t_data, "loss_first": float(losses[:20].mean()),
-                         "loss_last": float(losses[-50:].mean())}}
+                         "loss_last": float(losses[-50:].mean()),
+                         "samples_per_s": float(len(losses)) * 4096 / t_train,
+                         "tflops": float(len(losses)) * 4096 * MLP_TRAIN_FLOPS_PER_SAMPLE / t_train / 1e12,
+                         "gemms": "tcgen05 (BF16 operands, FP32 accumulators in tensor memory), batch 4096"}}
     if rk.rank == 0 and not args.no_poisson:
         line["poisson"] = surrogate_poisson(P, ctx, net, (1e-3, 3e-4, 1e-4, 3e-5))
     ctx.close()
     return line
+
+
+# BF16 GEMM flops of one training sample (2 per multiply-add): forward
+# 50(64 padded) -> 256 -> 256 -> 256 -> 25(32 padded), the backward data
+# products of the three upper layers, and the four weight gradients
+MLP_TRAIN_FLOPS_PER_SAMPLE = (2 * (64 * 256 + 2 * 256 * 256 + 256 * 32) + 2 * (32 * 256 + 2 * 256 * 256)
+                              + 2 * (32 * 256 + 2 * 256 * 256 + 256 * 64))
 
 
 def surrogate_poisson(P, ctx, net, taus, n_target=100_000, seed=7, reps=5):

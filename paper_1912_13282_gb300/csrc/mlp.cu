@@ -1,8 +1,8 @@
 // Learned surrogate of the Laplacian stencil weights (no counterpart in the
 // paper): a GELU multilayer perceptron 2n -> 256 -> 256 -> 256 -> n on the
 // scaled stencil offsets, BF16 weights/activations with FP32 accumulation on
-// the tensor cores (mma.sync m16n8k16), trained on weights the method itself
-// produces.  Its predictions are projected (double-FP32, or FP64) onto the rows
+// the tensor cores (tcgen05: the training GEMMs in gemm_tc.cu, the fused
+// inference in mlp_tc.cu), trained on weights the method itself produces.  Its predictions are projected (double-FP32, or FP64) onto the rows
 // Q^T w = l_q of the augmented system (Section 2.2.2, eq. rbf-system-aug), then
 // checked against the remaining rows' residual; rejected stencils get a solve.
 //
@@ -34,6 +34,11 @@ struct mm_mlp {
     float *Y = nullptr;                 // [bmax][32]
     __nv_bfloat16 *dY = nullptr;        // [bmax][32]
     __nv_bfloat16 *dZa = nullptr, *dZb = nullptr;   // [bmax][256]
+    // transposed copies for the tensor-core GEMMs, whose operands are K-major:
+    // weights [in][out] (W2..W4), activations / input / output gradient / dZ
+    // as [features][bmax]
+    __nv_bfloat16 *WT = nullptr, *HT = nullptr, *XT = nullptr, *dYT = nullptr;
+    __nv_bfloat16 *dZTa = nullptr, *dZTb = nullptr;
     float *loss = nullptr;              // [1]
     float *part = nullptr;              // [64][256][256] split-K / bias partial sums
     float *ymean = nullptr, *ystd = nullptr;   // [32] output scaling (device)
@@ -50,175 +55,22 @@ namespace {
 typedef __nv_bfloat16 bf16;
 constexpr int kH = 256, kKIN = 64, kKOUT = 32;
 
-// ------------------------------------------------------------------ GEMM
-// C[M x N] = A[M x K] * B^T with B given as [N x K]; either operand may be
-// stored K-contiguous ([m][k]) or M-contiguous ([k][m]).  Block tile 64 x 64 x
-// 32, four warps of 32 x 32, mma.sync m16n8k16 BF16 -> FP32.  K must be a
-// multiple of 8 and ld* multiples of 8 (16-byte vector loads); M, N arbitrary.
-constexpr int BM = 64, BN = 64, BK = 32, SPAD = 8;
-
-enum Epi { EPI_PARTIAL_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2, EPI_DGELU = 3 };
-
-struct EpiParams {
-    float *c;  int ldc; float alpha;   // EPI_PARTIAL_F32 (slice z at c + z*M*ldc) / EPI_BIAS_F32 output
-    const float *bias;                 // bias[n]
-    float *z;  int ldz;                // pre-activation (EPI_BIAS_GELU writes, EPI_DGELU reads)
-    bf16 *h;   int ldh;                // bf16 output (activation or dZ)
-};
-
-// GELU (tanh form) with the hardware tanh approximation, as in the fused
-// inference kernel
-__device__ __forceinline__ float tanh_hw(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float gelu_f(float z) {
-    const float c = 0.7978845608028654f;
-    return 0.5f * z * (1.0f + tanh_hw(c * fmaf(0.044715f * z, z * z, z)));
-}
-__device__ __forceinline__ float gelu_grad_f(float z) {
-    const float c = 0.7978845608028654f;
-    const float t = tanh_hw(c * fmaf(0.044715f * z, z * z, z));
-    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * z * z);
-}
-
-template <bool KMAJ>
-__device__ __forceinline__ void load_tile(bf16 (*S)[BK + SPAD], const bf16 *G, int ld, int r0, int k0,
-                                          int R, int K) {
-    const int tid = threadIdx.x;
-    if (KMAJ) {
-        // 64 rows x 32 k: 256 vectors of 8
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int v = tid + 128 * j, r = v >> 2, kc = (v & 3) * 8;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (r0 + r < R && k0 + kc < K) val = *reinterpret_cast<const uint4 *>(G + (int64_t)(r0 + r) * ld + k0 + kc);
-            *reinterpret_cast<uint4 *>(&S[r][kc]) = val;
-        }
-    } else {
-        // stored [k][r]: 32 k x 64 r, vectors of 8 along r, written transposed
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int v = tid + 128 * j, k = v >> 3, rc = (v & 7) * 8;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            const bool inb = k0 + k < K && r0 + rc < R;
-            if (inb && r0 + rc + 8 <= R) val = *reinterpret_cast<const uint4 *>(G + (int64_t)(k0 + k) * ld + r0 + rc);
-            const bf16 *e = reinterpret_cast<const bf16 *>(&val);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                bf16 x = e[i];
-                if (inb && r0 + rc + 8 > R) x = (r0 + rc + i < R) ? G[(int64_t)(k0 + k) * ld + r0 + rc + i] : __float2bfloat16(0.f);
-                S[rc + i][k] = x;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <bool AK, bool BKM, int EPI>
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *A, int lda,
-                                              const bf16 *B, int ldb, EpiParams ep, int kslice) {
-    __shared__ __align__(16) bf16 As[BM][BK + SPAD];
-    __shared__ __align__(16) bf16 Bs[BN][BK + SPAD];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        load_tile<AK>(As, A, lda, m0, k0, M, ke);
-        load_tile<BKM>(Bs, B, ldb, n0, k0, N, ke);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + g;
-                af[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
-                af[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
-                af[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t + 8]);
-                af[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int c = wn * 32 + nt * 8 + g;
-                bfr[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * t]);
-                bfr[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma16816(acc[mt][nt], af[mt], bfr[nt]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int r = m0 + wm * 32 + mt * 16 + g + 8 * h;
-                    const int c = n0 + wn * 32 + nt * 8 + 2 * t + q;
-                    if (r >= M || c >= N) continue;
-                    const float v = acc[mt][nt][2 * h + q];
-                    if (EPI == EPI_PARTIAL_F32) {
-                        ep.c[((int64_t)blockIdx.z * M + r) * ep.ldc + c] = ep.alpha * v;
-                    } else if (EPI == EPI_BIAS_GELU) {
-                        const float z = v + ep.bias[c];
-                        ep.z[(int64_t)r * ep.ldz + c] = z;
-                        ep.h[(int64_t)r * ep.ldh + c] = __float2bfloat16(gelu_f(z));
-                    } else if (EPI == EPI_BIAS_F32) {
-                        ep.c[(int64_t)r * ep.ldc + c] = v + ep.bias[c];
-                    } else {
-                        const float z = ep.z[(int64_t)r * ep.ldz + c];
-                        ep.h[(int64_t)r * ep.ldh + c] = __float2bfloat16(v * gelu_grad_f(z));
-                    }
-                }
-}
-
-template <bool AK, bool BKM, int EPI>
-int gemm(mm_ctx *ctx, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
-         const EpiParams &ep, int splits = 1, int *slices_out = nullptr) {
-    const int kslice = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (K + kslice - 1) / kslice);
-    k_gemm<AK, BKM, EPI><<<grid, 128, 0, ctx->stream>>>(M, N, K, A, lda, B, ldb, ep, kslice);
-    MM_LAUNCH_CHECK(ctx);
-    if (slices_out) *slices_out = (int)grid.z;
-    return MM_OK;
-}
-
 // ------------------------------------------------------------ elementwise
-__global__ void k_pack_x(const float *x, int64_t B, int n_in, bf16 *xb) {
+__global__ void k_pack_x(const float *x, int64_t B, int n_in, bf16 *xb, bf16 *xt, int64_t ldt) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * kKIN;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / kKIN;
         const int c = (int)(i % kKIN);
-        xb[i] = __float2bfloat16(c < n_in ? x[r * n_in + c] : 0.f);
+        const bf16 v = __float2bfloat16(c < n_in ? x[r * n_in + c] : 0.f);
+        xb[i] = v;
+        if (xt) xt[(int64_t)c * ldt + r] = v;
     }
 }
 
 // dY = 2 (Y - (T - mean)/std) / (B n_out) on the n_out real columns (0 in the
 // padding); loss += mean squared normalised error.
 __global__ void k_loss(const float *Y, const float *T, int64_t B, int n_out, const float *mean,
-                       const float *std, bf16 *dY, float *loss) {
+                       const float *std, bf16 *dY, bf16 *dYT, int64_t ldt, float *loss) {
     float s = 0.f;
     const float scale = 2.0f / ((float)B * n_out);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * kKOUT;
@@ -233,6 +85,7 @@ __global__ void k_loss(const float *Y, const float *T, int64_t B, int n_out, con
             s += e * e;
         }
         dY[i] = __float2bfloat16(d);
+        dYT[(int64_t)c * ldt + r] = __float2bfloat16(d);
     }
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, s / ((float)B * n_out));
@@ -269,6 +122,22 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t np,
         m[i] = mi;
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Transposed BF16 copies [in][out] of W2, W3 (256 x 256) and W4 (32 x 256),
+// the B operands of the backward GEMMs.
+__global__ void k_refresh_wt(const float *p, bf16 *wt, int64_t o2, int64_t o3, int64_t o4) {
+    const int64_t n2 = (int64_t)kH * kH, tot = 2 * n2 + (int64_t)kH * kKOUT;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = i, off;
+        int nout;
+        if (e < n2) { off = o2; nout = kH; }
+        else if ((e -= n2) < n2) { off = o3; nout = kH; }
+        else { e -= n2; off = o4; nout = kKOUT; }
+        const int64_t in = e / nout, out = e % nout;          // wt[in][out] = W[out][in]
+        wt[i] = __float2bfloat16(p[off + out * kH + in]);
     }
 }
 
@@ -309,15 +178,27 @@ const bf16 *wmat(const mm_mlp *net, int i) {
     return net->wb + off;
 }
 
-// dW = dZ^T H (split-K partial slices, then an ordered sum) and db = column
-// sums of dZ, both deterministic.
-int weight_grads(mm_ctx *ctx, mm_mlp *net, int out, int in, int64_t B, const bf16 *dZ,
-                 const bf16 *Hin, float *dW, float *db, int splits) {
-    EpiParams e{};
-    e.c = net->part; e.ldc = in; e.alpha = 1.f;
-    int slices = 1;
-    int rc = gemm<false, false, EPI_PARTIAL_F32>(ctx, out, in, (int)B, dZ, out, Hin, in, e, splits, &slices);
+// Transposed weight matrix i (1..3) inside WT, [in][out]
+const bf16 *wtmat(const mm_mlp *net, int i) {
+    return net->WT + (int64_t)(i - 1) * kH * kH;
+}
+
+// dW = dZ^T H on the tensor cores: A = dZ^T [out x B], B = H^T [in x B]
+// (both K-major, K = the B rows), split-K slices of `kslice` rows summed in
+// slice order, and db = column sums of dZ; both deterministic.
+int weight_grads(mm_ctx *ctx, mm_mlp *net, int out, int in, int64_t B, const bf16 *dZ, const bf16 *dZT,
+                 const bf16 *HinT, float *dW, float *db, int splits) {
+    TcGemmArgs a{};
+    a.M = out; a.N = in; a.K = (int)B;
+    a.kslice = (int)(((B + splits - 1) / splits + 63) / 64 * 64);
+    a.A = dZT; a.lda = net->bmax;
+    a.B = HinT; a.ldb = net->bmax;
+    a.epi = kTcPartial;
+    a.c = net->part; a.ldc = in;
+    a.err = net->tc_err;
+    int rc = tc_gemm(ctx, a);
     if (rc) return rc;
+    const int slices = (int)((B + a.kslice - 1) / a.kslice);
     k_sum_parts<<<grid1(ctx, (int64_t)out * in), 256, 0, ctx->stream>>>(net->part, slices, (int64_t)out * in, dW);
     const int nb = (int)std::min<int64_t>(B, 256);
     k_bias_partial<<<nb, out, 0, ctx->stream>>>(dZ, B, out, net->part);
@@ -326,27 +207,53 @@ int weight_grads(mm_ctx *ctx, mm_mlp *net, int out, int in, int64_t B, const bf1
     return MM_OK;
 }
 
-// Forward pass of `B` rows already packed in net->Xb; output in net->Y.
+// Forward pass of `B` rows already packed in net->Xb; output in net->Y.  Each
+// hidden layer writes its pre-activation, its activation and the transposed
+// activation (for the weight gradients).
 int forward(mm_ctx *ctx, mm_mlp *net, int64_t B) {
-    EpiParams ep{};
     const bf16 *in = net->Xb;
     int kin = kKIN;
     for (int l = 0; l < 3; ++l) {
-        ep.bias = net->p + net->ob[l];
-        ep.z = net->Z + (int64_t)l * net->bmax * kH;
-        ep.ldz = kH;
-        ep.h = net->Hb + (int64_t)l * net->bmax * kH;
-        ep.ldh = kH;
-        int rc = gemm<true, true, EPI_BIAS_GELU>(ctx, (int)B, kH, kin, in, kin, wmat(net, l), kin, ep);
+        TcGemmArgs a{};
+        a.M = (int)B; a.N = kH; a.K = kin; a.kslice = kin;
+        a.A = in; a.lda = kin;
+        a.B = wmat(net, l); a.ldb = kin;
+        a.epi = kTcBiasGelu;
+        a.bias = net->p + net->ob[l];
+        a.z = net->Z + (int64_t)l * net->bmax * kH; a.ldz = kH;
+        a.h = net->Hb + (int64_t)l * net->bmax * kH; a.ldh = kH;
+        a.ht = net->HT + (int64_t)l * net->bmax * kH; a.ldht = net->bmax;
+        a.err = net->tc_err;
+        int rc = tc_gemm(ctx, a);
         if (rc != MM_OK) return rc;
-        in = ep.h;
+        in = a.h;
         kin = kH;
     }
-    EpiParams eo{};
-    eo.c = net->Y;
-    eo.ldc = kKOUT;
-    eo.bias = net->p + net->ob[3];
-    return gemm<true, true, EPI_BIAS_F32>(ctx, (int)B, kKOUT, kH, in, kH, wmat(net, 3), kH, eo);
+    TcGemmArgs o{};
+    o.M = (int)B; o.N = kKOUT; o.K = kH; o.kslice = kH;
+    o.A = in; o.lda = kH;
+    o.B = wmat(net, 3); o.ldb = kH;
+    o.epi = kTcBias;
+    o.c = net->Y; o.ldc = kKOUT;
+    o.bias = net->p + net->ob[3];
+    o.err = net->tc_err;
+    return tc_gemm(ctx, o);
+}
+
+// dZ_prev = (dZ W) * gelu'(Z_prev) on the tensor cores: A = dZ [B x out],
+// B = W^T [in x out]; writes dZ_prev and its transpose.
+int backward_data(mm_ctx *ctx, mm_mlp *net, int64_t B, const bf16 *dZ, int out, const bf16 *WT, float *Zprev,
+                  bf16 *dZp, bf16 *dZpT) {
+    TcGemmArgs a{};
+    a.M = (int)B; a.N = kH; a.K = out; a.kslice = 64 * ((out + 63) / 64);
+    a.A = dZ; a.lda = out;
+    a.B = WT; a.ldb = out;
+    a.epi = kTcDGelu;
+    a.z = Zprev; a.ldz = kH;
+    a.h = dZp; a.ldh = kH;
+    a.ht = dZpT; a.ldht = net->bmax;
+    a.err = net->tc_err;
+    return tc_gemm(ctx, a);
 }
 
 // Gradients of the mean squared error w.r.t. all parameters into net->g
@@ -354,29 +261,29 @@ int forward(mm_ctx *ctx, mm_mlp *net, int64_t B) {
 int backward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *T) {
     cudaStream_t st = ctx->stream;
     k_loss<<<grid1(ctx, B * kKOUT), 256, 0, st>>>(net->Y, T, B, net->n_out, net->ymean, net->ystd,
-                                                   net->dY, net->loss);
+                                                   net->dY, net->dYT, net->bmax, net->loss);
     MM_LAUNCH_CHECK(ctx);
-    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 128));
     // output layer
-    const bf16 *H3 = net->Hb + 2 * net->bmax * kH;
-    int rc = weight_grads(ctx, net, kKOUT, kH, B, net->dY, H3, net->g + net->oW[3], net->g + net->ob[3], splits);
+    const bf16 *H3T = net->HT + 2 * net->bmax * kH;
+    int rc = weight_grads(ctx, net, kKOUT, kH, B, net->dY, net->dYT, H3T, net->g + net->oW[3],
+                          net->g + net->ob[3], splits);
     if (rc) return rc;
-    EpiParams ed{};
-    ed.z = net->Z + 2 * net->bmax * kH; ed.ldz = kH; ed.h = net->dZa; ed.ldh = kH;
-    rc = gemm<true, false, EPI_DGELU>(ctx, (int)B, kH, kKOUT, net->dY, kKOUT, wmat(net, 3), kH, ed);
+    rc = backward_data(ctx, net, B, net->dY, kKOUT, net->WT + 2 * (int64_t)kH * kH, net->Z + 2 * net->bmax * kH,
+                       net->dZa, net->dZTa);
     if (rc) return rc;
-    bf16 *dZ = net->dZa, *dZn = net->dZb;
+    bf16 *dZ = net->dZa, *dZn = net->dZb, *dZT = net->dZTa, *dZTn = net->dZTb;
     for (int l = 2; l >= 0; --l) {
-        const bf16 *Hin = l == 0 ? net->Xb : net->Hb + (int64_t)(l - 1) * net->bmax * kH;
+        const bf16 *HinT = l == 0 ? net->XT : net->HT + (int64_t)(l - 1) * net->bmax * kH;
         const int kin = l == 0 ? kKIN : kH;
-        rc = weight_grads(ctx, net, kH, kin, B, dZ, Hin, net->g + net->oW[l], net->g + net->ob[l], splits);
+        rc = weight_grads(ctx, net, kH, kin, B, dZ, dZT, HinT, net->g + net->oW[l], net->g + net->ob[l], splits);
         if (rc) return rc;
         if (l > 0) {
-            EpiParams eg{};
-            eg.z = net->Z + (int64_t)(l - 1) * net->bmax * kH; eg.ldz = kH; eg.h = dZn; eg.ldh = kH;
-            rc = gemm<true, false, EPI_DGELU>(ctx, (int)B, kH, kH, dZ, kH, wmat(net, l), kH, eg);
+            rc = backward_data(ctx, net, B, dZ, kH, wtmat(net, l), net->Z + (int64_t)(l - 1) * net->bmax * kH,
+                               dZn, dZTn);
             if (rc) return rc;
             std::swap(dZ, dZn);
+            std::swap(dZT, dZTn);
         }
     }
     return MM_OK;
@@ -386,6 +293,8 @@ int refresh_bf16(mm_ctx *ctx, mm_mlp *net) {
     const int64_t n1 = (int64_t)kH * kKIN, n2 = (int64_t)kH * kH, n4 = (int64_t)kKOUT * kH;
     k_refresh_bf16<<<grid1(ctx, n1 + 2 * n2 + n4), 256, 0, ctx->stream>>>(
         net->p, net->wb, net->oW[0], n1, net->oW[1], n2, net->oW[2], n2, net->oW[3], n4);
+    k_refresh_wt<<<grid1(ctx, 2 * n2 + n4), 256, 0, ctx->stream>>>(net->p, net->WT, net->oW[1], net->oW[2],
+                                                                   net->oW[3]);
     MM_LAUNCH_CHECK(ctx);
     const int rc = mlp_tc_image(ctx, net->p, net->oW, net->img);
     if (rc != MM_OK) return rc;
@@ -828,7 +737,9 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     const int64_t B = net->bmax;
     const size_t npart = (size_t)64 * kH * kH;
     size_t bytes_f = sizeof(float) * (size_t)(4 * off + 3 * B * kH + B * kKOUT + 1 + 2 * kKOUT + npart);
+    const int64_t wt_elems = 2 * (int64_t)kH * kH + (int64_t)kH * kKOUT;
     size_t bytes_h = sizeof(bf16) * (size_t)(wsz[0] + wsz[1] + wsz[2] + wsz[3] + 3 * B * kH + B * kKIN +
+                                             B * kKOUT + 2 * B * kH + wt_elems + 3 * B * kH + B * kKIN +
                                              B * kKOUT + 2 * B * kH + kMlpTcImageElems) + 256;
     char *fb = nullptr, *hb = nullptr;
     if (cudaMalloc(&fb, bytes_f) != cudaSuccess || cudaMalloc(&hb, bytes_h) != cudaSuccess) {
@@ -855,6 +766,12 @@ int mm_mlp_create(mm_ctx *ctx, mm_mlp **out, int n_in, int hidden, int n_layers,
     net->dY = h; h += B * kKOUT;
     net->dZa = h; h += B * kH;
     net->dZb = h; h += B * kH;
+    net->WT = h; h += wt_elems;
+    net->HT = h; h += 3 * B * kH;
+    net->XT = h; h += B * kKIN;
+    net->dYT = h; h += B * kKOUT;
+    net->dZTa = h; h += B * kH;
+    net->dZTb = h; h += B * kH;
     net->img = h; h += kMlpTcImageElems;     // offsets so far are multiples of 256 elements
     net->tc_err = (int *)h;
     // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases (plain layout)
@@ -970,7 +887,8 @@ int mm_mlp_forward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, float 
     }
     for (int64_t b0 = 0; b0 < B; b0 += net->bmax) {
         const int64_t bs = std::min(net->bmax, B - b0);
-        k_pack_x<<<grid1(ctx, bs * kKIN), 256, 0, ctx->stream>>>(d_x + b0 * net->n_in, bs, net->n_in, net->Xb);
+        k_pack_x<<<grid1(ctx, bs * kKIN), 256, 0, ctx->stream>>>(d_x + b0 * net->n_in, bs, net->n_in, net->Xb,
+                                                                  nullptr, 0);
         MM_LAUNCH_CHECK(ctx);
         int rc = forward(ctx, net, bs);
         if (rc != MM_OK) return rc;
@@ -987,7 +905,7 @@ int mm_mlp_grad(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, const flo
     ctx->err.clear();
     DeviceGuard g(ctx);
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(net->loss, 0, sizeof(float), ctx->stream));
-    k_pack_x<<<grid1(ctx, B * kKIN), 256, 0, ctx->stream>>>(d_x, B, net->n_in, net->Xb);
+    k_pack_x<<<grid1(ctx, B * kKIN), 256, 0, ctx->stream>>>(d_x, B, net->n_in, net->Xb, net->XT, net->bmax);
     MM_LAUNCH_CHECK(ctx);
     int rc = forward(ctx, net, B);
     if (rc == MM_OK) rc = backward(ctx, net, B, d_t);
@@ -1009,7 +927,7 @@ int mm_mlp_train_step(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, con
     DeviceGuard g(ctx);
     cudaStream_t st = ctx->stream;
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(net->loss, 0, sizeof(float), st));
-    k_pack_x<<<grid1(ctx, B * kKIN), 256, 0, st>>>(d_x, B, net->n_in, net->Xb);
+    k_pack_x<<<grid1(ctx, B * kKIN), 256, 0, st>>>(d_x, B, net->n_in, net->Xb, net->XT, net->bmax);
     MM_LAUNCH_CHECK(ctx);
     int rc = forward(ctx, net, B);
     if (rc == MM_OK) rc = backward(ctx, net, B, d_t);

@@ -107,6 +107,31 @@ constexpr int64_t kMlpTcImageElems = 16384 * 9 + 8192;   // W1 + W2 + W3 + W4 as
 int mlp_tc_image(mm_ctx *ctx, const float *p, const int64_t oW[4], __nv_bfloat16 *img);
 int mlp_tc_forward(mm_ctx *ctx, const MlpTcArgs &args);
 
+// Tensor-core GEMM of the MLP training (gemm_tc.cu): C[M x N] = A[M x K] *
+// B[N x K]^T, BF16 K-major operands (rows 16-byte aligned: leading dimensions
+// multiples of 8), FP32 accumulation, N <= 256, kslice (K per blockIdx.z) a
+// multiple of 64.
+enum { kTcPartial = 0, kTcBias = 1, kTcBiasGelu = 2, kTcDGelu = 3 };
+struct TcGemmArgs {
+    int M, N, K, kslice;
+    const __nv_bfloat16 *A;
+    int64_t lda;
+    const __nv_bfloat16 *B;
+    int64_t ldb;
+    int epi;
+    float *c;              // kTcPartial: slice z at c + z*M*ldc; kTcBias: output
+    int64_t ldc;
+    const float *bias;     // [N]
+    float *z;              // pre-activation: written by kTcBiasGelu, read by kTcDGelu
+    int64_t ldz;
+    __nv_bfloat16 *h;      // BF16 row-major output (activation or dZ)
+    int64_t ldh;
+    __nv_bfloat16 *ht;     // optional BF16 transposed output [N x ldht]
+    int64_t ldht;
+    int *err;              // set to 1 if a wait timed out
+};
+int tc_gemm(mm_ctx *ctx, const TcGemmArgs &a);
+
 int weights_launch(mm_ctx *ctx, const WeightsJob &job, int precision);
 // FP32 + refinement kernel of one class (2D / 3D); handed-over rows go to fb_list
 int mixed_launch_2d(mm_ctx *ctx, const WeightsJob &job, int *fb_count, int *fb_list);
