@@ -25,9 +25,12 @@ Other workloads (--workload):
   wls        GWLS weights (Section 2.2.1) on the 10^6-node disk.
   poisson    the implicit Poisson solve (Section 2.3.2) on a 2*10^4-node
              disk: assembly, ILU(0), BiCGSTAB.
+  square     the small configuration: 10,201 nodes on the unit square, n=12
+             r^3 deg 2, FP64 and FP32+IR, every row against the oracle,
+             Dirichlet Poisson through the GPU implicit solve.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload disk|ball|batch|surrogate|wls|poisson]
+                       [--workload disk|ball|batch|surrogate|wls|poisson|square]
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own
 independent node set (seed = rank): weak scaling, no data-path collective;
 the step time is the maximum over ranks.
@@ -69,7 +72,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="disk", choices=["disk", "ball", "batch", "surrogate", "wls", "poisson"])
+    ap.add_argument("--workload", default="disk", choices=["disk", "ball", "batch", "surrogate", "wls", "poisson",
+                                                          "square"])
     ap.add_argument("--n-target", type=int, default=None, help="override the node count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -1189,6 +1193,107 @@ def surrogate_poisson(P, ctx, net, taus, n_target=100_000, seed=7, reps=5):
     return out
 
 
+# ------------------------------------------------------------ unit square
+SQUARE = {"workload": "unit square, h = 0.01 (10,201 nodes, jittered interior, Dirichlet edges): n=12 PHS r^3 + "
+                      "deg-2 monomials, lap/dx/dy on every node; Poisson u = sin(pi x) sin(pi y) solved with the "
+                      "GPU implicit solve",
+          "h": 0.01, "n": 12, "k": 3, "m": 2, "ops": 1 | 2 | 4}
+
+
+def run_square(args, rk):
+    """The small configuration: whole step (kNN + weights of every node + 3
+    operator applications) in FP64 and in the FP32 + refinement form, the
+    weights' error against the oracle on every row, and the Dirichlet Poisson
+    error of both weight sets through the GPU implicit solve."""
+    import torch
+
+    import nodesets as NS
+    import paper_1912_13282_gb300 as P
+    device = rk.local
+    stream = torch.cuda.current_stream(device)
+    ctx = P.Context(device, stream)
+    ns = NS.square(SQUARE["h"], seed=rk.rank)
+    n, k, m, ops = SQUARE["n"], SQUARE["k"], SQUARE["m"], SQUARE["ops"]
+    N = ns.N
+    dv = f"cuda:{device}"
+    pts = torch.from_numpy(ns.pts).to(dv)
+    rp_h = np.arange(N + 1, dtype=np.int64) * n
+    rp = torch.from_numpy(rp_h).to(dv)
+    col = torch.empty(N * n, dtype=torch.int32, device=dv)
+    vals = [torch.zeros(N * n, dtype=torch.float64, device=dv) for _ in range(3)]
+    u = torch.from_numpy(NS.sin_product(ns.pts)).to(dv)
+    y = torch.empty_like(u)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dv)
+
+    def step(prec):
+        ctx.knn_stencils(pts, [(0, N, n, col)], method=P.KNN_GRID)
+        ctx.rbffd_weights(ops, k, m, pts, rp, col, vals, n_max=n, precision=prec)
+        for v in vals:
+            ctx.apply_operator(rp, col, v, u, y)
+
+    for _ in range(max(3, args.warmup)):
+        step(P.FP64)
+        step(P.FP32_IR)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    res = {}
+    for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        rk.barrier()
+        ts = []
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(prec)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        (ms,) = rk.max([float(np.sum(ts))])
+        (n_all,) = rk.sum([N])
+        res[name] = {"ms_per_step": ms / args.steps, "value": throughput(n_all, ms, args.steps)}
+    clk = clocks.stop()
+    # accuracy: every row against the oracle, and the Poisson error of both weight sets
+    out_err, poisson = {}, {}
+    kind = torch.from_numpy(ns.dirichlet.astype(np.uint8)).to(dv)
+    rhs = np.where(ns.dirichlet, NS.sin_product(ns.pts), NS.sin_product_lap(ns.pts))
+    b = torch.from_numpy(rhs).to(dv)
+    for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        step(prec)
+        torch.cuda.synchronize()
+        if rk.rank == 0 and not args.no_error:
+            from oracle import oracle as O
+            ref, st, _ = O.weights(ns.pts, rp_h, col.cpu().numpy(), k, m, ops, nthreads=O.nthreads_default())
+            errs = []
+            for r in range(3):
+                g = vals[r].cpu().numpy().reshape(N, n)
+                w = ref[r].reshape(N, n)
+                errs.append(float((np.abs(g - w).max(1) / np.abs(w).max(1)).max()))
+            out_err[name] = {"max_rel_err_lap_dx_dy": errs, "rows": N}
+        cs, vs = torch.empty_like(col), torch.empty_like(vals[0])
+        ctx.implicit_assemble(rp, col, vals[0], kind, cs, vs)
+        f = torch.empty_like(vs)
+        diag = torch.empty(N, dtype=torch.int64, device=dv)
+        ctx.ilu0(rp, cs, vs, f, diag)
+        x = torch.zeros(N, dtype=torch.float64, device=dv)
+        rc, it, rr = ctx.bicgstab(rp, cs, vs, b, x, f, diag, tol=1e-12, maxit=5000)
+        poisson[name] = {"max_error": float(np.abs(x.cpu().numpy() - NS.sin_product(ns.pts)).max()),
+                         "bicgstab_iterations": it, "converged": rc == P.binding.MM_OK}
+    poisson["relative_difference"] = abs(poisson["fp32_ir"]["max_error"] - poisson["fp64"]["max_error"]) / \
+        poisson["fp64"]["max_error"]
+    line = {"metric": METRIC, "value": res["fp64"]["value"], "unit": "nodes/s", "n_gpus": rk.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["fp64"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": SQUARE["workload"], "N": N,
+                       "l2": "256 MiB buffer written between timed steps",
+                       "note": "10^4 nodes: the step is launch-bound (16 launches)"},
+            "fp64_plain": res["fp64"], "fp32_ir": res["fp32_ir"], "error": out_err, "poisson": poisson,
+            "clocks": clk, "gpu_launches": 16 * args.steps * 2}
+    ctx.close()
+    return line
+
+
 # ------------------------------------------------------- implicit Poisson
 POISSON = {"workload": "implicit Poisson solve (Section 2.3.2, the benchmark problem of Section 5) on the "
                        "disk minus 5 holes, 2e4 nodes: interior Laplacian rows n=25 r^5 deg 4, Dirichlet "
@@ -1367,7 +1472,7 @@ def main(argv=None):
         _build.build()
     rk.barrier()
     run = {"disk": run_disk, "ball": run_ball, "batch": run_batch, "surrogate": run_surrogate,
-           "wls": run_wls, "poisson": run_poisson}[args.workload]
+           "wls": run_wls, "poisson": run_poisson, "square": run_square}[args.workload]
     line = run(args, rk)
     if rk.rank == 0:
         print(json.dumps(line), flush=True)
