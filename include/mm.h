@@ -121,8 +121,9 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value);
  * is owned by the context and valid until its next call. */
 const char *mm_last_error(const mm_ctx *ctx);
 
-/* Bytes of device workspace the context holds now (0 until a call needed
- * one; it only grows, and is freed by mm_ctx_destroy); -1 for NULL. */
+/* Bytes of device workspace the context holds now, over its buffers (0
+ * until a call needed one; they only grow, and are freed by mm_ctx_destroy);
+ * -1 for NULL. */
 int64_t mm_ctx_workspace_bytes(const mm_ctx *ctx);
 
 /* -------------------------------------------------------------- stencils */
@@ -152,6 +153,25 @@ typedef struct {
  */
 int mm_knn_stencils(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
                     const mm_knn_range *ranges, int method, int32_t *d_status);
+
+/*
+ * Balanced stencils (Section 3.1: FindBalancedSupport "also ensures that
+ * stencils are balanced around the central node"; the paper gives no rule,
+ * this is the library's reading).  For every query node c of a range: the K
+ * closest nodes (the ranking of mm_knn_stencils, c first) are the candidates;
+ * a candidate j lies in the orthant o(j) = sum_a 2^a [x_j,a - x_c,a < 0]
+ * (2^dim orthants); each orthant contributes its first (n - 1) / 2^dim
+ * candidates (integer division) in ranking order; the remaining slots go to
+ * the closest candidates not taken.  Row q lists c, then the n - 1 taken
+ * candidates in ranking order.  With K = n the result is mm_knn_stencils'.
+ *   ranges   as mm_knn_stencils (n per range), 1 <= n <= K.
+ *   K        candidates per query, n <= K <= 64, K <= N.
+ *   d_status optional: as mm_knn_stencils.
+ * Uses a second context buffer of (query rows) x K int32 for the candidates.
+ * Errors: MM_EBADARG, MM_EUNSUPPORTED (K > 64), MM_ENOMEM, MM_ECUDA.
+ */
+int mm_balanced_stencils(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
+                         const mm_knn_range *ranges, int K, int method, int32_t *d_status);
 
 /* ------------------------------------------------------------ CSR pattern */
 /* Device CSR stencil pattern: row i spans col[row_ptr[i] .. row_ptr[i+1]-1]. */

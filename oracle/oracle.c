@@ -16,6 +16,9 @@
  *   orc_knn_brute           Section 2.1 (stencils of the n closest nodes, the
  *                           node itself first); exhaustive search, ranked by
  *                           (squared distance in FP64, node index).
+ *   orc_balanced_brute      Section 3.1 (FindBalancedSupport, stencils balanced
+ *                           around the node): a quota per orthant among the K
+ *                           nearest candidates, then the nearest of the rest.
  *   orc_rbffd_weights       Section 2.2.2, eq. rbf-system-aug and the RHS
  *                           definitions around it; Section 3.3 (weights for
  *                           all nodes and operators stored per operator).
@@ -275,6 +278,60 @@ int orc_knn_brute(int dim, int64_t N, const double *pts, int64_t nq, const int64
     knn_job J = {dim, N, pts, queries, n, idx, status};
     orc_parallel_for(nthreads, 0, nq, knn_body, &J);
     return ORC_OK;
+}
+
+/*
+ * Balanced stencils (Section 3.1 names FindBalancedSupport: stencils "balanced
+ * around the central node"; the paper states no rule, this is the reading the
+ * library implements).  For query c: the K nearest nodes (orc_knn_brute's
+ * ranking, c first) are the candidates; every other candidate j lies in the
+ * orthant o(j) = sum_a 2^a [x_j,a - x_c,a < 0]; with quota = (n - 1) / 2^dim
+ * (integer division) the candidates are scanned in ranking order and j is
+ * taken if fewer than `quota` earlier candidates of o(j) were taken; then,
+ * while fewer than n - 1 are taken, the not-yet-taken candidates are added in
+ * ranking order.  The row is c followed by the taken candidates in ranking
+ * order.  status as orc_knn_brute (ORC_BADARG also when K < n or N < K).
+ */
+int orc_balanced_brute(int dim, int64_t N, const double *pts, int64_t nq, const int64_t *queries,
+                       int n, int K, int32_t *idx, int32_t *status, int nthreads)
+{
+    if (dim < 1 || dim > ORC_MAXDIM || n < 1 || K < n || K > 64 || N < 1) return ORC_BADARG;
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nq > 0 ? nq : 1) * (size_t)K);
+    if (!cand) return ORC_NOMEM;
+    int rc = orc_knn_brute(dim, N, pts, nq, queries, K, cand, status, nthreads);
+    const int quota = (n - 1) / (1 << dim);
+    for (int64_t q = 0; rc == ORC_OK && q < nq; ++q) {
+        const int32_t *cq = cand + q * K;
+        int32_t *out = idx + q * n;
+        const int64_t c = cq[0];
+        int taken[64 + 1] = {0};
+        int per[8] = {0};
+        int count = 0;
+        for (int t = 1; t < K && count < n - 1; ++t) {
+            if (cq[t] < 0) break;
+            int o = 0;
+            for (int a = 0; a < dim; ++a)
+                if (pts[(int64_t)cq[t] * dim + a] - pts[c * dim + a] < 0.0) o |= 1 << a;
+            if (per[o] < quota) {
+                per[o] += 1;
+                taken[t] = 1;
+                ++count;
+            }
+        }
+        for (int t = 1; t < K && count < n - 1; ++t)
+            if (cq[t] >= 0 && !taken[t]) {
+                taken[t] = 1;
+                ++count;
+            }
+        out[0] = (int32_t)c;
+        int w = 1;
+        for (int t = 1; t < K && w < n; ++t)
+            if (taken[t]) out[w++] = cq[t];
+        for (; w < n; ++w) out[w] = -1;
+        if (status && status[q] == ORC_OK && count < n - 1) status[q] = ORC_BADARG;
+    }
+    free(cand);
+    return rc;
 }
 
 /* ------------------------------------------------------------ batch weights */

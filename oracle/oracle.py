@@ -55,6 +55,9 @@ def _load():
     lib.orc_monomial_table.restype = C.c_int
     lib.orc_knn_brute.argtypes = [C.c_int, i64, C.c_void_p, i64, C.c_void_p, C.c_int,
                                   C.c_void_p, C.c_void_p, C.c_int]
+    lib.orc_balanced_brute.argtypes = [C.c_int, i64, C.c_void_p, i64, C.c_void_p, C.c_int, C.c_int,
+                                       C.c_void_p, C.c_void_p, C.c_int]
+    lib.orc_balanced_brute.restype = C.c_int
     lib.orc_knn_brute.restype = C.c_int
     wargs = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, i64, i64, C.c_int,
              C.c_int, u32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
@@ -144,6 +147,21 @@ def knn(pts: np.ndarray, n: int, queries=None, nthreads: int = 1):
     rc = lib.orc_knn_brute(dim, N, _ptr(pts), len(q), _ptr(q), n, _ptr(idx), _ptr(st), nthreads)
     if rc != OK:
         raise ValueError(f"orc_knn_brute rc={rc}")
+    return idx, st
+
+
+def balanced(pts: np.ndarray, n: int, K: int, queries=None, nthreads: int = 1):
+    """Balanced stencils of n nodes among the K nearest candidates
+    (orc_balanced_brute): (idx [nq, n] int32, status [nq] int32)."""
+    lib = _load()
+    pts = _c(pts, np.float64)
+    N, dim = pts.shape
+    q = np.arange(N, dtype=np.int64) if queries is None else _c(queries, np.int64)
+    idx = np.empty((len(q), n), dtype=np.int32)
+    st = np.empty(len(q), dtype=np.int32)
+    rc = lib.orc_balanced_brute(dim, N, _ptr(pts), len(q), _ptr(q), n, K, _ptr(idx), _ptr(st), nthreads)
+    if rc != OK:
+        raise ValueError(f"orc_balanced_brute rc={rc}")
     return idx, st
 
 

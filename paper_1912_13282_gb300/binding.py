@@ -37,7 +37,7 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
            "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights", "mm_diffuse_bc",
            "mm_combine_operators", "mm_implicit_assemble", "mm_ilu0", "mm_ilu0_solve", "mm_bicgstab",
-           "mm_partition_morton", "mm_partition_halo"]
+           "mm_partition_morton", "mm_partition_halo", "mm_balanced_stencils"]
 
 
 class KnnRange(C.Structure):
@@ -94,6 +94,8 @@ def load():
         lib.mm_ctx_workspace_bytes.argtypes = [vp]
         lib.mm_knn_stencils.argtypes = [vp, C.c_int, i64, vp, C.c_int, C.POINTER(KnnRange),
                                         C.c_int, vp]
+        lib.mm_balanced_stencils.argtypes = [vp, C.c_int, i64, vp, C.c_int, C.POINTER(KnnRange), C.c_int,
+                                             C.c_int, vp]
         lib.mm_rbffd_weights.argtypes = [vp, C.c_uint, C.c_int, C.c_int, C.c_int, i64, vp, vp,
                                          C.POINTER(CsrPattern), i64, i64, C.c_int, C.c_int,
                                          C.POINTER(vp), vp]
@@ -221,6 +223,22 @@ class Context:
             _dev(status, "status", torch.int32)
         self._check(self._lib.mm_knn_stencils(self._h, dim, N, _ptr(pts), len(ranges), arr,
                                               method, _ptr(status)))
+
+    def balanced_stencils(self, pts: torch.Tensor, ranges, K: int, method: int = KNN_AUTO,
+                          status: torch.Tensor | None = None):
+        """mm_balanced_stencils; ranges as knn_stencils, K candidates per query."""
+        _dev(pts, "pts", torch.float64)
+        N, dim = pts.shape
+        arr = (KnnRange * max(1, len(ranges)))()
+        for i, (qb, qe, n, out) in enumerate(ranges):
+            _dev(out, "idx", torch.int32)
+            if out.numel() < (qe - qb) * n:
+                raise MMError("idx tensor too small")
+            arr[i] = KnnRange(qb, qe, n, out.data_ptr())
+        if status is not None:
+            _dev(status, "status", torch.int32)
+        self._check(self._lib.mm_balanced_stencils(self._h, dim, N, _ptr(pts), len(ranges), arr, int(K),
+                                                   method, _ptr(status)))
 
     # ------------------------------------------------------------- weights
     def rbffd_weights(self, ops: int, k: int, m: int, pts: torch.Tensor, row_ptr: torch.Tensor,

@@ -82,6 +82,24 @@ char *mm_workspace(mm_ctx *ctx, size_t bytes) {
     return ctx->ws;
 }
 
+char *mm_workspace2(mm_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws2_bytes) return ctx->ws2;
+    size_t want = bytes + bytes / 4 + (1 << 20);
+    if (ctx->ws2) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->ws2);
+        ctx->ws2 = nullptr;
+        ctx->ws2_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->ws2, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws2 = nullptr;
+        return nullptr;
+    }
+    ctx->ws2_bytes = want;
+    return ctx->ws2;
+}
+
 cudaError_t mm_set_smem(const mm_ctx *ctx, const void *kernel, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<int, const void *>, size_t> done;
@@ -194,6 +212,7 @@ void mm_ctx_destroy(mm_ctx *ctx) {
     DeviceGuard g(ctx);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->ws2) cudaFree(ctx->ws2);
     delete ctx;
 }
 
@@ -239,7 +258,9 @@ int mm_ctx_set_option(mm_ctx *ctx, int key, double value) {
 
 const char *mm_last_error(const mm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int64_t mm_ctx_workspace_bytes(const mm_ctx *ctx) { return ctx ? (int64_t)ctx->ws_bytes : -1; }
+int64_t mm_ctx_workspace_bytes(const mm_ctx *ctx) {
+    return ctx ? (int64_t)(ctx->ws_bytes + ctx->ws2_bytes) : -1;
+}
 
 int mm_knn_stencils(mm_ctx *ctx, int dim, int64_t N, const double *d_pts, int nranges,
                     const mm_knn_range *ranges, int method, int32_t *d_status) {

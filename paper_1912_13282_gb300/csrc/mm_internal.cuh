@@ -21,6 +21,10 @@ struct mm_ctx {
     // growable device workspace (bump-allocated per call)
     char *ws = nullptr;
     size_t ws_bytes = 0;
+    // a second growable buffer for calls that hold data across another
+    // call's use of the workspace (the candidates of the balanced stencils)
+    char *ws2 = nullptr;
+    size_t ws2_bytes = 0;
     // options
     double ir_tol = 1e-9;
     int ir_max_steps = 4;
@@ -47,6 +51,8 @@ int mm_warps_per_block(const mm_ctx *ctx, const void *kernel, size_t bytes_per_w
 
 // Ensures the workspace holds at least `bytes`; returns its base or nullptr.
 char *mm_workspace(mm_ctx *ctx, size_t bytes);
+// The same for the second buffer.
+char *mm_workspace2(mm_ctx *ctx, size_t bytes);
 
 // Bump allocator over the workspace, 256-byte aligned slices.
 struct WsCarve {
