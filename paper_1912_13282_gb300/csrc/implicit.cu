@@ -261,6 +261,93 @@ __global__ void k_fill_pending(int64_t n, double *x) {
         reinterpret_cast<unsigned long long *>(x)[i] = kPending;
 }
 
+// ------------------------------------------------------- dependency levels
+// Level of every row in a substitution: 0 without dependencies, else 1 + the
+// largest level of the rows it reads (lower: columns < i of its row, upper:
+// columns > i).  Sync-free like the substitutions (ticket order, each level a
+// readiness flag: -1 until written); *maxlev receives the largest level.
+template <bool LOWER>
+__global__ void __launch_bounds__(256) k_levels(int64_t nrows, const int64_t *__restrict__ rp,
+                                                const int32_t *__restrict__ col,
+                                                const int64_t *__restrict__ diag, int32_t *lev, int32_t *maxlev,
+                                                unsigned long long *tickets, int slot, int *err) {
+    reset_next_ticket(tickets, slot);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const int64_t t = next_ticket(tickets + slot);
+        if (t >= nrows) break;
+        const int64_t i = LOWER ? t : nrows - 1 - t;
+        const int64_t b = LOWER ? __ldg(rp + i) : __ldg(diag + i) + 1;
+        const int64_t e = LOWER ? __ldg(diag + i) : __ldg(rp + i + 1);
+        int m = -1;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            const int k = __ldg(col + p);
+            int v;
+            asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(lev + k) : "memory");
+            for (uint32_t it = 0; v < 0; ++it) {
+                if (it >= kSpinMax) {
+                    atomicExch(err, 1);
+                    v = 0;
+                    break;
+                }
+                if (it > 32) __nanosleep(32);
+                asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(lev + k) : "memory");
+            }
+            m = max(m, v);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(lev + i), "r"(m + 1) : "memory");
+            atomicMax(maxlev, m + 1);
+        }
+    }
+}
+
+// Counting sort of the rows by level: counts, exclusive prefix (one block),
+// scatter (the order inside a level is arbitrary: each row's arithmetic does
+// not depend on it).
+__global__ void k_level_count(int64_t nrows, const int32_t *__restrict__ lev, int32_t *count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(count + lev[i], 1);
+}
+__global__ void __launch_bounds__(1024) k_level_scan(const int32_t *maxlev, int32_t *count) {
+    __shared__ int32_t part[32];
+    const int nl = *maxlev + 1;
+    int32_t carry = 0;
+    for (int base = 0; base < nl; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int32_t v = i < nl ? count[i] : 0;
+        int32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) part[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int32_t w = part[threadIdx.x];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (threadIdx.x >= o) w += y;
+            }
+            part[threadIdx.x] = w;
+        }
+        __syncthreads();
+        const int32_t before = (threadIdx.x >= 32 ? part[(threadIdx.x >> 5) - 1] : 0) + x - v;
+        if (i < nl) count[i] = carry + before;   // exclusive start of level i
+        const int32_t tot = part[31];
+        __syncthreads();
+        carry += tot;
+    }
+}
+__global__ void k_level_scatter(int64_t nrows, const int32_t *__restrict__ lev, int32_t *start, int32_t *order) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x)
+        order[atomicAdd(start + lev[i], 1)] = (int32_t)i;
+}
+
 // ------------------------------------------------------- BiCGSTAB scalars
 struct KrylovScalars {
     double rho, rho1, alpha, omega, beta, nb, res, tol;
@@ -282,8 +369,8 @@ __global__ void __launch_bounds__(256) k_lower(int64_t nrows, const int64_t *__r
                                                const int64_t *__restrict__ diag, const double *bvec,
                                                double *pv, const double *__restrict__ r,
                                                const double *__restrict__ v, const KrylovScalars *sc,
-                                               double *y, double *x_reset, unsigned long long *tickets,
-                                               int slot, int *err) {
+                                               double *y, double *x_reset, const int32_t *__restrict__ order,
+                                               unsigned long long *tickets, int slot, int *err) {
     reset_next_ticket(tickets, slot);
     if (sc && sc->stop) return;
     const int lane = threadIdx.x & 31;
@@ -291,8 +378,9 @@ __global__ void __launch_bounds__(256) k_lower(int64_t nrows, const int64_t *__r
     if (RHS == kRhsP) { c1 = sc->beta; c2 = sc->omega; }
     if (RHS == kRhsS) c1 = sc->alpha;
     for (;;) {
-        const int64_t i = next_ticket(tickets + slot);
-        if (i >= nrows) break;
+        const int64_t t = next_ticket(tickets + slot);
+        if (t >= nrows) break;
+        const int64_t i = order ? (int64_t)__ldg(order + t) : t;
         const int64_t b = __ldg(rp + i), dg = __ldg(diag + i);
         const int nl = (int)(dg - b);
         double acc = 0.0;
@@ -327,6 +415,7 @@ __global__ void __launch_bounds__(256) k_upper(int64_t nrows, const int64_t *__r
                                                const double *__restrict__ F,
                                                const int64_t *__restrict__ diag, double *y, double *x,
                                                bool reset_y, const KrylovScalars *sc,
+                                               const int32_t *__restrict__ order,
                                                unsigned long long *tickets, int slot, int *err) {
     reset_next_ticket(tickets, slot);
     if (sc && sc->stop) return;
@@ -334,7 +423,7 @@ __global__ void __launch_bounds__(256) k_upper(int64_t nrows, const int64_t *__r
     for (;;) {
         const int64_t t = next_ticket(tickets + slot);
         if (t >= nrows) break;
-        const int64_t i = nrows - 1 - t;
+        const int64_t i = order ? (int64_t)__ldg(order + t) : nrows - 1 - t;
         const int64_t dg = __ldg(diag + i), e = __ldg(rp + i + 1);
         const int nu = (int)(e - dg - 1);
         double acc = 0.0;
@@ -559,7 +648,8 @@ int read_err(mm_ctx *ctx, const int *d_err, const char *what) {
     return mm_fail(ctx, MM_ECUDA, "%s: error %d", what, e);
 }
 
-// Workspace of the solves: err, tickets, scalars, partials, flags, vectors.
+// Workspace of the solves: err, tickets, scalars, partials, flags, vectors,
+// and (with levels) the rows of the two substitutions sorted by dependency level.
 struct KrylovWs {
     int *err;
     unsigned long long *tickets;
@@ -567,15 +657,19 @@ struct KrylovWs {
     double *partials;
     uint32_t *flag;
     double *vec[9];   // r, rh, p, v, ph, s, sh, t, Y
+    int32_t *lev, *count, *maxlev, *ordL, *ordU;
 };
 
-int krylov_ws(mm_ctx *ctx, int64_t n, int nparts, int nvec, bool flags, KrylovWs *w) {
+int krylov_ws(mm_ctx *ctx, int64_t n, int nparts, int nvec, bool flags, KrylovWs *w, bool levels = false) {
     WsCarve c;
     const size_t o_err = c.take<int>(1), o_tk = c.take<unsigned long long>(kTickets),
                  o_sc = c.take<KrylovScalars>(1), o_part = c.take<double>(2 * (size_t)nparts),
                  o_flag = c.take<uint32_t>(flags ? (size_t)n : 1);
     size_t o_vec[9];
     for (int i = 0; i < nvec; ++i) o_vec[i] = c.take<double>((size_t)n);
+    const size_t nl = levels ? (size_t)n : 1;
+    const size_t o_lev = c.take<int32_t>(nl), o_cnt = c.take<int32_t>(nl + 1), o_max = c.take<int32_t>(1),
+                 o_ordL = c.take<int32_t>(nl), o_ordU = c.take<int32_t>(nl);
     char *ws = mm_workspace(ctx, c.off);
     if (!ws) return mm_fail(ctx, MM_ENOMEM, "solver workspace of %zu bytes", c.off);
     w->err = (int *)(ws + o_err);
@@ -584,6 +678,11 @@ int krylov_ws(mm_ctx *ctx, int64_t n, int nparts, int nvec, bool flags, KrylovWs
     w->partials = (double *)(ws + o_part);
     w->flag = (uint32_t *)(ws + o_flag);
     for (int i = 0; i < nvec; ++i) w->vec[i] = (double *)(ws + o_vec[i]);
+    w->lev = (int32_t *)(ws + o_lev);
+    w->count = (int32_t *)(ws + o_cnt);
+    w->maxlev = (int32_t *)(ws + o_max);
+    w->ordL = levels ? (int32_t *)(ws + o_ordL) : nullptr;
+    w->ordU = levels ? (int32_t *)(ws + o_ordU) : nullptr;
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(ws, 0, o_part, ctx->stream));   // err, tickets, scalars
     if (flags) MM_CUDA_CHECK(ctx, cudaMemsetAsync(w->flag, 0, (size_t)n * sizeof(uint32_t), ctx->stream));
     return MM_OK;
@@ -601,11 +700,35 @@ void precond(mm_ctx *ctx, const mm_csr_pattern *A, const double *F, const int64_
              const KrylovWs &w, int &seq, int lblocks, int ublocks) {
     const int64_t n = A->nrows;
     k_lower<RHS><<<lblocks, 256, 0, ctx->stream>>>(n, A->d_row_ptr, A->d_col, F, diag, b, pv, r, v, sc, Y, x,
-                                                   w.tickets, seq % kTickets, w.err);
+                                                   w.ordL, w.tickets, seq % kTickets, w.err);
     ++seq;
-    k_upper<<<ublocks, 256, 0, ctx->stream>>>(n, A->d_row_ptr, A->d_col, F, diag, Y, x, true, sc, w.tickets,
-                                              seq % kTickets, w.err);
+    k_upper<<<ublocks, 256, 0, ctx->stream>>>(n, A->d_row_ptr, A->d_col, F, diag, Y, x, true, sc, w.ordU,
+                                              w.tickets, seq % kTickets, w.err);
     ++seq;
+}
+
+// The rows of both substitutions sorted by dependency level (ordL, ordU), so
+// the tickets hand out the rows of one wavefront together.
+template <bool LOWER>
+void sort_by_level(mm_ctx *ctx, const mm_csr_pattern *A, const int64_t *diag, const KrylovWs &w, int &seq,
+                   int32_t *order) {
+    const int64_t n = A->nrows;
+    cudaStream_t st = ctx->stream;
+    cudaMemsetAsync(w.lev, 0xFF, sizeof(int32_t) * (size_t)n, st);
+    cudaMemsetAsync(w.count, 0, sizeof(int32_t) * (size_t)(n + 1), st);
+    cudaMemsetAsync(w.maxlev, 0, sizeof(int32_t), st);
+    const int lb = ticket_blocks(ctx, (const void *)k_levels<LOWER>, n);
+    k_levels<LOWER><<<lb, 256, 0, st>>>(n, A->d_row_ptr, A->d_col, diag, w.lev, w.maxlev, w.tickets,
+                                        seq % kTickets, w.err);
+    ++seq;
+    k_level_count<<<vec_blocks(ctx, n), kVecThreads, 0, st>>>(n, w.lev, w.count);
+    k_level_scan<<<1, 1024, 0, st>>>(w.maxlev, w.count);
+    k_level_scatter<<<vec_blocks(ctx, n), kVecThreads, 0, st>>>(n, w.lev, w.count, order);
+}
+
+void sort_levels(mm_ctx *ctx, const mm_csr_pattern *A, const int64_t *diag, const KrylovWs &w, int &seq) {
+    sort_by_level<true>(ctx, A, diag, w, seq, w.ordL);
+    sort_by_level<false>(ctx, A, diag, w, seq, w.ordU);
 }
 
 }  // namespace
@@ -656,10 +779,11 @@ extern "C" int mm_ilu0_solve(mm_ctx *ctx, const mm_csr_pattern *A, const double 
         return mm_fail(ctx, MM_EBADARG, "factors, diag, b and a distinct x are required");
     DeviceGuard g(ctx);
     KrylovWs w{};
-    if (int rc = krylov_ws(ctx, A->nrows, 1, 1, false, &w)) return rc;
+    if (int rc = krylov_ws(ctx, A->nrows, 1, 1, false, &w, true)) return rc;
     double *Y = w.vec[0];
     fill_pending(ctx, Y, A->nrows);
     int seq = 0;
+    sort_levels(ctx, A, d_diag, w, seq);
     const int lb = ticket_blocks(ctx, (const void *)k_lower<kRhsPlain>, A->nrows);
     const int ub = ticket_blocks(ctx, (const void *)k_upper, A->nrows);
     precond<kRhsPlain>(ctx, A, d_factors, d_diag, d_b, nullptr, nullptr, nullptr, nullptr, Y, d_x, w, seq, lb, ub);
@@ -680,7 +804,7 @@ extern "C" int mm_bicgstab(mm_ctx *ctx, const mm_csr_pattern *A, const double *d
     const int64_t n = A->nrows;
     const int nb = vec_blocks(ctx, n);
     KrylovWs w{};
-    if (int rc = krylov_ws(ctx, n, nb, 9, false, &w)) return rc;
+    if (int rc = krylov_ws(ctx, n, nb, 9, false, &w, d_factors != nullptr)) return rc;
     double *r = w.vec[0], *rh = w.vec[1], *p = w.vec[2], *v = w.vec[3], *ph = w.vec[4], *s = w.vec[5],
            *shv = w.vec[6], *t = w.vec[7], *Y = w.vec[8];
     const bool pre = d_factors != nullptr;
@@ -699,6 +823,7 @@ extern "C" int mm_bicgstab(mm_ctx *ctx, const mm_csr_pattern *A, const double *d
     const int lb = pre ? ticket_blocks(ctx, (const void *)k_lower<kRhsP>, n) : 0;
     const int ub = pre ? ticket_blocks(ctx, (const void *)k_upper, n) : 0;
     int seq = 0;
+    if (pre) sort_levels(ctx, A, d_diag, w, seq);
     constexpr int kCheck = 16;   // iterations enqueued between two looks at the scalars
     KrylovScalars h{};
     for (int done = 0; done < maxit; done += kCheck) {
