@@ -3,7 +3,7 @@
 // u <- u + dt L u on internal rows (eq. exp-start .. exp-end: Dirichlet rows
 // held, Neumann rows solved from their own d/dn row), and the general
 // second-order operator as a per-node combination of derivative weights
-// (eq. gen-op).
+// (eq. gen-op, one warp per 32 rows streaming their entries flat).
 //
 // A group of G lanes (G a power of two, chosen from the mean row length)
 // handles a row: the lanes read consecutive value/column entries of the row
@@ -125,23 +125,40 @@ struct CombineArgs {
     const double *coef[kMaxTerms];
 };
 
-template <int G>
+// One warp per 32 consecutive rows: the rows' pointers in one coalesced load,
+// then the rows' entries as one flat range, 32 consecutive entries per step
+// (every load coalesced and independent of the others); a lane finds the
+// row of its entry among the 32 pointers by a shuffle binary search and
+// reads that row's coefficients (cached).  Bound by HBM traffic: (T + 1) x 8
+// bytes per entry plus the coefficients.
 __global__ void __launch_bounds__(256) k_combine(int64_t row_begin, int64_t row_end, const int64_t *__restrict__ rp,
                                                  const __grid_constant__ CombineArgs A, double *out) {
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int sub = threadIdx.x & (G - 1);
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    for (int64_t row = row_begin + tid / G; row < row_end; row += ngroups) {
-        double a[kMaxTerms];
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = row_begin + (((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5); r0 < row_end;
+         r0 += nw * 32) {
+        const int nr = (int)(row_end - r0 < 32 ? row_end - r0 : 32);
+        // lane l holds the start of row r0 + l (lanes past the block: the end)
+        const int64_t start = __ldg(rp + r0 + min(lane, nr));
+        const int64_t e_all = __ldg(rp + r0 + nr);
+        const int64_t b_all = __shfl_sync(0xffffffffu, start, 0);
+        for (int64_t e = b_all + lane; e - lane < e_all; e += 32) {
+            // the largest row index q in [0, nr) with start(q) <= e
+            int q = 0;
 #pragma unroll
-        for (int t = 0; t < kMaxTerms; ++t) a[t] = t < A.nterms ? (A.coef[t] ? __ldg(A.coef[t] + row) : 1.0) : 0.0;
-        const int64_t b = __ldg(rp + row), e = __ldg(rp + row + 1);
-        for (int64_t p = b + sub; p < e; p += G) {
-            double s = 0.0;
+            for (int step = 16; step; step >>= 1) {
+                const int cand = q + step;
+                const int64_t sc = __shfl_sync(0xffffffffu, start, cand < 32 ? cand : 31);
+                if (cand < nr && sc <= e) q = cand;
+            }
+            if (e < e_all) {
+                const int64_t row = r0 + q;
+                double s = 0.0;
 #pragma unroll
-            for (int t = 0; t < kMaxTerms; ++t)
-                if (t < A.nterms) s = fma(a[t], A.term[t][p], s);
-            out[p] = s;
+                for (int t = 0; t < kMaxTerms; ++t)
+                    if (t < A.nterms) s = fma(A.coef[t] ? __ldg(A.coef[t] + row) : 1.0, __ldg(A.term[t] + e), s);
+                out[e] = s;
+            }
         }
     }
 }
@@ -183,10 +200,9 @@ int combine_launch(mm_ctx *ctx, const mm_csr_pattern *p, int64_t row_begin, int6
         A.term[t] = terms[t];
         A.coef[t] = coefs ? coefs[t] : nullptr;
     }
-    const int G = 4;
     const int64_t rows = row_end - row_begin;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * G + 255) / 256, (int64_t)ctx->num_sms * 8));
-    k_combine<G><<<blocks, 256, 0, ctx->stream>>>(row_begin, row_end, p->d_row_ptr, A, out);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, (int64_t)ctx->num_sms * 8));
+    k_combine<<<blocks, 256, 0, ctx->stream>>>(row_begin, row_end, p->d_row_ptr, A, out);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }
