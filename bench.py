@@ -79,6 +79,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--no-poisson", action="store_true")
+    ap.add_argument("--train-samples", type=int, default=1 << 20, help="surrogate: training stencils")
+    ap.add_argument("--train-epochs", type=int, default=120, help="surrogate: training epochs")
     return ap.parse_args(argv)
 
 
@@ -634,7 +636,9 @@ def run_disk(args, rk):
     traffic = stored_traffic("k_weights_mixed<2,2,3,40>")
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": None if traffic is None else traffic["bytes_per_row"] * Ni,
+            "traffic": None if traffic is None else traffic.get("full_size", traffic)["bytes_per_row"] * Ni,
+            "traffic_source": "profiles/traffic.json: one-pass ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                              "of this launch on this workload, per row x rows",
             "kernel": "k_weights_mixed<2,2,3,40> (interior rows; FP32 Gauss-Jordan inverse with the "
                       "rows in registers + double-FP32 refinement)",
             "algorithmic": "the method's flops per interior stencil, (2/3)M^3 + 2RM^2 + 8n(n-1)/2 + 4nl "
@@ -1038,7 +1042,7 @@ def run_surrogate(args, rk):
     device = rk.local
     ctx = P.Context(device, torch.cuda.current_stream(device))
     n, k, m = 25, 5, 4
-    ntrain = 1 << 20
+    ntrain = args.train_samples
     neval = args.n_target or 1_000_000
     t0 = time.time()
     data = S.make_dataset(ctx, ntrain, seed=1 + 1000 * rk.rank)
@@ -1046,7 +1050,7 @@ def run_surrogate(args, rk):
     t_data = time.time() - t0
     net = P.MLP(ctx, 2 * n, n, seed=rk.rank)
     t0 = time.time()
-    losses = S.train(net, data["x"], data["t"], epochs=120, batch=4096, lr=3e-3, lr_final=1e-4)
+    losses = S.train(net, data["x"], data["t"], epochs=args.train_epochs, batch=4096, lr=3e-3, lr_final=1e-4)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del data
@@ -1093,7 +1097,7 @@ def run_surrogate(args, rk):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["surir"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32+f64", "data": "synthetic",
-            "config": {"workload": f"surrogate: MLP 50-256x3-25 trained (120 epochs) on {ntrain} jittered-patch "
+            "config": {"workload": f"surrogate: MLP 50-256x3-25 trained ({args.train_epochs} epochs) on {ntrain} jittered-patch "
                                    f"stencils, {neval} held-out stencils (n=25, r^5, deg 4)",
                        "tau": tau},
             "fp64_plain": res["fp64"], "fp32_ir": res["ir"], "surrogate_fp64_fallback": res["sur"],
