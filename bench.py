@@ -81,6 +81,7 @@ def parse(argv=None):
     ap.add_argument("--no-poisson", action="store_true")
     ap.add_argument("--train-samples", type=int, default=1 << 20, help="surrogate: training stencils")
     ap.add_argument("--train-epochs", type=int, default=120, help="surrogate: training epochs")
+    ap.add_argument("--train-batch", type=int, default=4096, help="surrogate: training batch (<= 65536)")
     return ap.parse_args(argv)
 
 
@@ -480,6 +481,7 @@ def poisson_comparison(P, ctx, device, n_target=100_000):
         torch.cuda.synchronize()
         out[name] = poisson_error(ns, rp, pipe.col.cpu().numpy(), pipe.op.cpu().numpy())
     out["N"] = ns.N
+    out["note"] = "a smaller instance of the same disk workload (the host direct solve is untimed)"
     out["relative_difference"] = abs(out["fp32_ir"] - out["fp64"]) / out["fp64"]
     out["equal_within_1pct"] = out["relative_difference"] <= 0.01
     return out
@@ -1050,7 +1052,8 @@ def run_surrogate(args, rk):
     t_data = time.time() - t0
     net = P.MLP(ctx, 2 * n, n, seed=rk.rank)
     t0 = time.time()
-    losses = S.train(net, data["x"], data["t"], epochs=args.train_epochs, batch=4096, lr=3e-3, lr_final=1e-4)
+    losses = S.train(net, data["x"], data["t"], epochs=args.train_epochs, batch=args.train_batch, lr=3e-3,
+                     lr_final=1e-4)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del data
@@ -1112,9 +1115,10 @@ def run_surrogate(args, rk):
             "training": {"samples": ntrain, "steps": int(len(losses)), "seconds": t_train,
                          "data_seconds": t_data, "loss_first": float(losses[:20].mean()),
                          "loss_last": float(losses[-50:].mean()),
-                         "samples_per_s": float(len(losses)) * 4096 / t_train,
-                         "tflops": float(len(losses)) * 4096 * MLP_TRAIN_FLOPS_PER_SAMPLE / t_train / 1e12,
-                         "gemms": "tcgen05 (BF16 operands, FP32 accumulators in tensor memory), batch 4096"}}
+                         "samples_per_s": float(len(losses)) * args.train_batch / t_train,
+                         "tflops": float(len(losses)) * args.train_batch * MLP_TRAIN_FLOPS_PER_SAMPLE / t_train / 1e12,
+                         "gemms": "tcgen05 (BF16 operands, FP32 accumulators in tensor memory), batch %d"
+                                  % args.train_batch}}
     if rk.rank == 0 and not args.no_poisson:
         line["poisson"] = surrogate_poisson(P, ctx, net, (1e-3, 3e-4, 1e-4, 3e-5))
     ctx.close()

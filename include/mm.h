@@ -498,6 +498,16 @@ int mm_mlp_set_params(mm_ctx *ctx, mm_mlp *net, const float *h_params);
 int mm_mlp_get_params(mm_ctx *ctx, const mm_mlp *net, float *h_params);
 /* Output scaling: targets are learned as (y - mean[c]) / std[c]; host arrays [n_out]. */
 int mm_mlp_set_output_scaling(mm_ctx *ctx, mm_mlp *net, const float *h_mean, const float *h_std);
+/* The same from training targets d_t [B x n_out] (device): per column the mean
+ * and the standard deviation (B - 1 in the denominator, at least 1e-6), two
+ * passes in a fixed order.  Synchronises. */
+int mm_mlp_fit_output_scaling(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_t);
+/* Training targets of the surrogate: the weights of rows [row_begin,
+ * row_end) (n entries each) in scaled units, d_out[(i - row_begin) n + j] =
+ * d_vals[row_ptr[i] + j] * d_scale[i - row_begin]^q as FP32 (q = 2 for the
+ * Laplacian; d_scale from mm_stencil_features).  Errors: MM_EBADARG. */
+int mm_surrogate_targets(mm_ctx *ctx, const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end, int n,
+                         const double *d_vals, const double *d_scale, int q, float *d_out);
 /* d_y [B x n_out] = network(d_x [B x n_in]) (FP32 in and out, scaling undone).
  * By default one fused tensor-core kernel (tcgen05, activations kept on chip);
  * MM_OPT_MLP_INFER = MM_MLP_LAYERED runs the layer-by-layer training path.  A

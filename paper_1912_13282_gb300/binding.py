@@ -37,7 +37,8 @@ EXPORTS = ["mm_ctx_create", "mm_ctx_destroy", "mm_ctx_set_stream", "mm_ctx_set_o
            "mm_mlp_forward", "mm_mlp_train_step", "mm_mlp_grad", "mm_mlp_save", "mm_mlp_load",
            "mm_stencil_features", "mm_rbffd_weights_surrogate", "mm_wls_weights", "mm_diffuse_bc",
            "mm_combine_operators", "mm_implicit_assemble", "mm_ilu0", "mm_ilu0_solve", "mm_bicgstab",
-           "mm_partition_morton", "mm_partition_halo", "mm_balanced_stencils"]
+           "mm_partition_morton", "mm_partition_halo", "mm_balanced_stencils",
+           "mm_mlp_fit_output_scaling", "mm_surrogate_targets"]
 
 
 class KnnRange(C.Structure):
@@ -118,6 +119,8 @@ def load():
         lib.mm_mlp_get_params.argtypes = [vp, vp, vp]
         lib.mm_mlp_set_output_scaling.argtypes = [vp, vp, vp, vp]
         lib.mm_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        lib.mm_mlp_fit_output_scaling.argtypes = [vp, vp, i64, vp]
+        lib.mm_surrogate_targets.argtypes = [vp, C.POINTER(CsrPattern), i64, i64, C.c_int, vp, vp, C.c_int, vp]
         lib.mm_mlp_train_step.argtypes = [vp, vp, i64, vp, vp, C.c_float, vp]
         lib.mm_mlp_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         lib.mm_mlp_save.argtypes = [vp, vp, C.c_char_p]
@@ -571,6 +574,11 @@ class MLP:
                                                              m.ctypes.data_as(C.c_void_p),
                                                              s.ctypes.data_as(C.c_void_p)))
 
+    def fit_output_scaling(self, t: torch.Tensor):
+        """mm_mlp_fit_output_scaling from training targets t [B, n_out] (device)."""
+        _dev(t, "t", torch.float32)
+        self.ctx._check(self._lib.mm_mlp_fit_output_scaling(self.ctx._h, self._h, t.shape[0], _ptr(t)))
+
     def forward(self, x: torch.Tensor, y: torch.Tensor):
         _dev(x, "x", torch.float32)
         _dev(y, "y", torch.float32)
@@ -606,6 +614,16 @@ def stencil_features(ctx: Context, pts, row_ptr, col, row_begin, row_end, n, x, 
     ctx._check(ctx._lib.mm_stencil_features(ctx._h, pts.shape[1], pts.shape[0], _ptr(pts),
                                             C.byref(pat), row_begin, row_end, n, int(orient),
                                             _ptr(x), _ptr(scale)))
+
+
+def surrogate_targets(ctx: Context, row_ptr, row_begin, row_end, n, vals, scale, q, out):
+    """mm_surrogate_targets: out [(row_end - row_begin), n] FP32 = vals * scale^q."""
+    _dev(vals, "vals", torch.float64)
+    _dev(scale, "scale", torch.float64)
+    _dev(out, "out", torch.float32)
+    pat = CsrPattern(row_ptr.numel() - 1, vals.numel(), row_ptr.data_ptr(), 0)
+    ctx._check(ctx._lib.mm_surrogate_targets(ctx._h, C.byref(pat), row_begin, row_end, n, _ptr(vals),
+                                             _ptr(scale), q, _ptr(out)))
 
 
 def rbffd_weights_surrogate(ctx: Context, net: MLP, k, m, pts, row_ptr, col, row_begin, row_end, n,

@@ -863,6 +863,93 @@ int mm_mlp_set_output_scaling(mm_ctx *ctx, mm_mlp *net, const float *h_mean, con
     return MM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Column mean and standard deviation (n - 1 in the denominator, floored at
+// 1e-6) of t [B x ncol]: one block per column, two passes, block sums in a
+// fixed order.
+__global__ void __launch_bounds__(256) k_column_stats(const float *t, int64_t B, int ncol, float *mean,
+                                                      float *std) {
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < B; r += blockDim.x) s += (double)t[r * ncol + c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double mu = sh[0] / (double)B;
+    __syncthreads();
+    double v = 0.0;
+    for (int64_t r = threadIdx.x; r < B; r += blockDim.x) {
+        const double d = (double)t[r * ncol + c] - mu;
+        v += d * d;
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mean[c] = (float)mu;
+        std[c] = fmaxf((float)sqrt(sh[0] / (double)(B > 1 ? B - 1 : 1)), 1e-6f);
+    }
+}
+
+// Weights of rows [r0, r1) (n entries each) in scaled units, w s^q, as FP32
+__global__ void k_scaled_targets(const int64_t *rp, const double *vals, const double *scale, int64_t r0,
+                                 int64_t r1, int n, int q, float *out) {
+    const int64_t total = (r1 - r0) * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n;
+        const int j = (int)(e - i * n);
+        const double s = scale[i];
+        double f = 1.0;
+        for (int t = 0; t < q; ++t) f *= s;
+        out[e] = (float)(vals[rp[r0 + i] + j] * f);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mm_mlp_fit_output_scaling(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_t) {
+    if (!ctx || !net || B < 1 || !d_t) return MM_EBADARG;
+    ctx->err.clear();
+    DeviceGuard g(ctx);
+    k_column_stats<<<net->n_out, 256, 0, ctx->stream>>>(d_t, B, net->n_out, net->ymean, net->ystd);
+    MM_LAUNCH_CHECK(ctx);
+    // host copies (checkpoints carry them)
+    MM_CUDA_CHECK(ctx, cudaMemcpyAsync(net->h_mean.data(), net->ymean, sizeof(float) * net->n_out,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+    MM_CUDA_CHECK(ctx, cudaMemcpyAsync(net->h_std.data(), net->ystd, sizeof(float) * net->n_out,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_surrogate_targets(mm_ctx *ctx, const mm_csr_pattern *stencils, int64_t row_begin, int64_t row_end, int n,
+                         const double *d_vals, const double *d_scale, int q, float *d_out) {
+    if (!ctx) return MM_EBADARG;
+    ctx->err.clear();
+    if (!stencils || !stencils->d_row_ptr || row_begin < 0 || row_end < row_begin || row_end > stencils->nrows ||
+        n < 1 || q < 0 || q > 4 || !d_vals || !d_scale || !d_out)
+        return mm_fail(ctx, MM_EBADARG, "bad arguments to mm_surrogate_targets");
+    if (row_end == row_begin) return MM_OK;
+    DeviceGuard g(ctx);
+    const int64_t total = (row_end - row_begin) * n;
+    k_scaled_targets<<<grid1(ctx, total), 256, 0, ctx->stream>>>(stencils->d_row_ptr, d_vals, d_scale, row_begin,
+                                                                 row_end, n, q, d_out);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
 int mm_mlp_forward(mm_ctx *ctx, mm_mlp *net, int64_t B, const float *d_x, float *d_y) {
     if (!ctx || !net || B < 0 || (B > 0 && (!d_x || !d_y))) return MM_EBADARG;
     ctx->err.clear();

@@ -3,15 +3,15 @@
 Stencils come from jittered grid patches (one patch per stencil, jitter
 amplitude U(0, 0.3 h) per patch): the library's kNN picks the 25 nearest
 nodes of each patch centre, the library's FP64 solver gives the exact
-weights (PHS r^5 + degree-4 monomials), and the library's feature kernel the
-scaled offsets.  Targets are the weights in scaled units, w_s = w * s^2.
+weights (PHS r^5 + degree-4 monomials), the library's feature kernel the
+scaled offsets, and mm_surrogate_targets the weights in scaled units,
+w_s = w * s^2 (the targets); the output scaling is fitted on the GPU.
 Training runs the library's BF16 forward/backward kernels and Adam.
 """
 from __future__ import annotations
 
 import math
 
-import numpy as np
 import torch
 
 import nodesets as NS
@@ -41,10 +41,10 @@ def make_dataset(ctx: B.Context, count: int, seed: int, n: int = 25, k: int = 5,
     x = torch.empty((count, 2 * n), dtype=torch.float32, device="cuda")
     s = torch.empty(count, dtype=torch.float64, device="cuda")
     B.stencil_features(ctx, pts, rp, col, 0, count, n, x, s)
-    ws = vals.view(count, n) * (s * s)[:, None]
+    t = torch.empty((count, n), dtype=torch.float32, device="cuda")
+    B.surrogate_targets(ctx, rp, 0, count, n, vals, s, 2, t)
     ok = status == B.ST_OK
-    return {"x": x[ok].contiguous(), "t64": ws[ok].contiguous(),
-            "t": ws[ok].to(torch.float32).contiguous(), "pts": pts, "row_ptr": rp, "col": col,
+    return {"x": x[ok].contiguous(), "t": t[ok].contiguous(), "pts": pts, "row_ptr": rp, "col": col,
             "status": status}
 
 
@@ -52,9 +52,7 @@ def train(net: B.MLP, x: torch.Tensor, t: torch.Tensor, epochs: int = 4, batch: 
           lr: float = 2e-3, lr_final: float = 1e-4, seed: int = 0, log_every: int = 0):
     """Adam with cosine-decayed learning rate over shuffled minibatches;
     returns the per-step losses (read back once at the end)."""
-    mean = t.mean(0).double().cpu().numpy()
-    std = t.std(0).double().cpu().numpy()
-    net.set_output_scaling(mean, np.maximum(std, 1e-6))
+    net.fit_output_scaling(t)
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     N = x.shape[0]

@@ -184,6 +184,37 @@ def test_fused_inference_matches_layered(P, ctx, B):
     net.close()
 
 
+def test_targets_and_output_scaling_on_gpu(P, ctx):
+    """mm_surrogate_targets (w s^2 per row, FP32) and mm_mlp_fit_output_scaling
+    (column mean and standard deviation, n - 1 denominator) against numpy."""
+    rng = np.random.default_rng(7)
+    rows, n = 3000, N_OUT
+    rp = torch.arange(rows + 1, dtype=torch.int64, device="cuda") * n
+    vals = torch.from_numpy(rng.normal(size=rows * n)).cuda()
+    scale = torch.from_numpy(rng.uniform(0.01, 0.1, size=rows - 100)).cuda()
+    out = torch.full((rows - 100, n), float("nan"), dtype=torch.float32, device="cuda")
+    P.binding.surrogate_targets(ctx, rp, 50, rows - 50, n, vals, scale, 2, out)
+    torch.cuda.synchronize()
+    v = vals.cpu().numpy().reshape(rows, n)[50:rows - 50]
+    ref = (v * scale.cpu().numpy()[:, None] ** 2).astype(np.float32)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    net = P.MLP(ctx, N_IN, N_OUT, seed=1)
+    t = torch.from_numpy((rng.normal(size=(5000, N_OUT)) * 3 + 1).astype(np.float32)).cuda()
+    net.fit_output_scaling(t)
+    th = t.cpu().numpy().astype(np.float64)
+    mean, std = th.mean(0), th.std(0, ddof=1)
+    y = torch.empty((1, N_OUT), device="cuda")
+    # the scaling is what the network undoes: zero weights and biases but an
+    # output bias of 1 give y = 1 * std + mean
+    p = np.zeros(net.num_params, dtype=np.float32)
+    p[-N_OUT:] = 1.0
+    net.set_params(p)
+    net.forward(torch.zeros((1, N_IN), device="cuda"), y)
+    torch.cuda.synchronize()
+    assert np.allclose(y.cpu().numpy()[0], mean + std, rtol=1e-5, atol=1e-5), (y, mean + std)
+    net.close()
+
+
 def test_params_and_checkpoint_roundtrip(P, ctx, tmp_path):
     net = P.MLP(ctx, N_IN, N_OUT, seed=5)
     rng = np.random.default_rng(1)
