@@ -383,7 +383,11 @@ int mm_diffuse(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals
  * d_u or d_work.  A centre weight of 0 gives a non-finite value.  The update
  * divides by the centre d/dn weight, so with one-sided stencils whose centre
  * weight is small against the others, coupled Neumann nodes amplify errors
- * from step to step.  Errors: as mm_diffuse.
+ * from step to step.  A sufficient condition for them not to: over the
+ * Neumann rows i, max_i sum_{j >= 2, node j Neumann} |w_ij| / |w_i1| < 1 (the
+ * Neumann values' update is then a contraction in the max norm); on the
+ * one-sided stencils around holes of a disk this ratio can exceed 10^2, and
+ * the scheme is then unstable whatever dt.  Errors: as mm_diffuse.
  */
 int mm_diffuse_bc(mm_ctx *ctx, const mm_csr_pattern *stencils, const double *d_vals,
                   const uint8_t *d_kind, const double *d_g, double dt, int steps, double *d_u,
