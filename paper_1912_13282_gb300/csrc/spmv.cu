@@ -6,50 +6,65 @@
 // (eq. gen-op, one warp per 32 rows streaming their entries flat).
 //
 // A group of G lanes (G a power of two, chosen from the mean row length)
-// handles a row: the lanes read consecutive value/column entries of the row
-// (coalesced), gather u, and reduce with shuffles inside the group.  The
-// kernel is bound by HBM traffic: 12 bytes per nonzero (value + column), the
-// row pointer, the y write, and the u gather (mostly cache hits when stencil
-// neighbours have nearby indices).
+// handles a row: the lanes read interleaved value/column entries of the row
+// (all of a lane's entries of a batch at once), gather u, and reduce with
+// shuffles inside the group.  The traffic is 12 bytes per nonzero (value +
+// column), the row pointer, the y write and the u gather (mostly cache hits
+// when stencil neighbours have nearby indices); on GB300 the FP64 pipe (one
+// multiply-add per nonzero) bounds it about as much as HBM does.
 #include <algorithm>
 
 #include "mm_internal.cuh"
 
 namespace {
 
-// A group of G lanes takes RB consecutive rows per iteration, their loads
-// interleaved, so several independent chains of dependent loads (row pointer,
-// value/column, gathered u) are in flight per group.  Narrow groups (4 lanes
-// for stencil rows of 10-48 nonzeros: one 32-byte sector of values per load)
-// measured best on the 1e6-node disk operator: 3.2 TB/s against 1.4 TB/s
-// with 16 lanes per row.
-constexpr int RB = 2;
+// A group of G lanes takes RB consecutive rows per iteration; lane `sub`
+// handles the row's entries sub, sub + G, sub + 2G, ... (cnt of them) in
+// batches: it issues all value and column loads of a batch, then all gathers
+// of u, then the multiply-adds in entry order, so a row costs three dependent
+// memory round trips (row pointer, value/column, u).  Batches of 8, then one
+// of 4, 2 and 1 as the lane's remaining count allows, so no multiply-add is
+// issued for an entry that does not exist: GB300's FP64 pipe (~1/64 of the
+// FP32 rate) is the bound of this kernel, one FP64 warp instruction per
+// entry batch step plus log2(G) for the group's shuffle reduction, so two
+// lanes per row (one reduction step, rows of 25-30 entries split 13/12 or
+// 15/15) issue few FP64 instructions per row while a load instruction still
+// reads 16-byte runs of a row.  Measured on the 1e6-node disk operator (3
+// applications): 4 lanes per row 0.299 ms, 2 lanes 0.248 ms, one lane per
+// row (uncoalesced row reads) 0.399 ms.
+constexpr int RB = 1;
+
+template <int NB, int G>
+__device__ __forceinline__ void dot_batch(int64_t p, const int32_t *__restrict__ col, const double *__restrict__ val,
+                                          const double *__restrict__ u, double &acc) {
+    int c[NB];
+    double v[NB], x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        c[k] = __ldg(col + p + (int64_t)G * k);
+        v[k] = __ldg(val + p + (int64_t)G * k);
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) x[k] = __ldg(u + c[k]);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(v[k], x[k], acc);
+}
 
 template <int G>
 __device__ __forceinline__ void rows_dot(int64_t base, int64_t nrows, int sub, const int64_t *__restrict__ rp,
                                          const int32_t *__restrict__ col, const double *__restrict__ val,
                                          const double *__restrict__ u, double (&acc)[RB]) {
-    int64_t b[RB], e[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-        const bool in = base + r < nrows;
-        b[r] = in ? __ldg(rp + base + r) : 0;
-        e[r] = in ? __ldg(rp + base + r + 1) : 0;
         acc[r] = 0.0;
-    }
-    int64_t p[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) p[r] = b[r] + sub;
-    bool more = true;
-    while (more) {
-        more = false;
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-            if (p[r] < e[r]) {
-                acc[r] = fma(__ldg(val + p[r]), __ldg(u + __ldg(col + p[r])), acc[r]);
-                p[r] += G;
-                more |= p[r] < e[r];
-            }
+        if (base + r >= nrows) continue;
+        const int64_t b = __ldg(rp + base + r), e = __ldg(rp + base + r + 1);
+        int64_t p = b + sub;
+        int64_t cnt = e > p ? (e - p + G - 1) / G : 0;
+        for (; cnt >= 8; cnt -= 8, p += 8 * G) dot_batch<8, G>(p, col, val, u, acc[r]);
+        if (cnt >= 4) { dot_batch<4, G>(p, col, val, u, acc[r]); cnt -= 4; p += 4 * G; }
+        if (cnt >= 2) { dot_batch<2, G>(p, col, val, u, acc[r]); cnt -= 2; p += 2 * G; }
+        if (cnt >= 1) dot_batch<1, G>(p, col, val, u, acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -73,7 +88,7 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t nrows, const int64_t *__re
         for (int r = 0; r < RB; ++r)
             if (r % G == sub && base + r < nrows) {
                 const int64_t row = base + r;
-                y[row] = beta == 0.0 ? alpha * acc[r] : fma(alpha, acc[r], beta * y[row]);
+                y[row] = beta == 0.0 ? (alpha == 1.0 ? acc[r] : alpha * acc[r]) : fma(alpha, acc[r], beta * y[row]);
             }
     }
 }
@@ -165,13 +180,16 @@ __global__ void __launch_bounds__(256) k_combine(int64_t row_begin, int64_t row_
 
 int group_for(const mm_csr_pattern *p) {
     double avg = p->nrows > 0 ? (double)p->nnz / (double)p->nrows : 1.0;
-    return avg >= 48 ? 8 : 4;
+    return avg >= 96 ? 4 : 2;
 }
 
-// one wave at full occupancy (8 blocks of 256 threads per SM), fewer for small matrices
-int grid_for(mm_ctx *ctx, int64_t nrows, int G) {
+// one wave at the kernel's occupancy (blocks of 256 threads), fewer for small matrices
+int grid_for(mm_ctx *ctx, int64_t nrows, int G, const void *kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
     int64_t need = ((nrows + RB - 1) / RB * G + 255) / 256;
-    int64_t cap = (int64_t)ctx->num_sms * 8;
+    int64_t cap = (int64_t)ctx->num_sms * per_sm;
     return (int)std::max<int64_t>(1, std::min(need, cap));
 }
 
@@ -181,11 +199,11 @@ int spmv_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, const 
                 double alpha, double beta, double *y) {
     if (p->nrows == 0) return MM_OK;
     const int G = group_for(p);
-    const int blocks = grid_for(ctx, p->nrows, G);
+    const int blocks = grid_for(ctx, p->nrows, G, G == 4 ? (const void *)k_spmv<4> : (const void *)k_spmv<2>);
     cudaStream_t st = ctx->stream;
     switch (G) {
-        case 8: k_spmv<8><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, u, alpha, beta, y); break;
-        default: k_spmv<4><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, u, alpha, beta, y); break;
+        case 4: k_spmv<4><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, u, alpha, beta, y); break;
+        default: k_spmv<2><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, u, alpha, beta, y); break;
     }
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
@@ -211,13 +229,14 @@ int diffuse_launch(mm_ctx *ctx, const mm_csr_pattern *p, const double *vals, con
                    const double *g, int neumann, double dt, int steps, double *u, double *work) {
     if (p->nrows == 0 || steps <= 0) return MM_OK;
     const int G = group_for(p);
-    const int blocks = grid_for(ctx, p->nrows, G);
+    const int blocks = grid_for(ctx, p->nrows, G,
+                                G == 4 ? (const void *)k_diffuse_step<4> : (const void *)k_diffuse_step<2>);
     cudaStream_t st = ctx->stream;
     double *src = u, *dst = work;
     for (int t = 0; t < steps; ++t) {
         switch (G) {
-            case 8: k_diffuse_step<8><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, g, neumann, src, dt, dst); break;
-            default: k_diffuse_step<4><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, g, neumann, src, dt, dst); break;
+            case 4: k_diffuse_step<4><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, g, neumann, src, dt, dst); break;
+            default: k_diffuse_step<2><<<blocks, 256, 0, st>>>(p->nrows, p->d_row_ptr, p->d_col, vals, fixed, g, neumann, src, dt, dst); break;
         }
         MM_LAUNCH_CHECK(ctx);
         double *t2 = src; src = dst; dst = t2;
