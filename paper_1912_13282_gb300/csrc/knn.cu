@@ -43,6 +43,7 @@ struct GridParams {
     int ncells;
     float lo32[3];     // FP32 copies for the conservative tests
     float cell32;
+    float inv_cell32;  // FP32 1/cell: ring centre of a query (any cell is a valid centre)
     float delta32;     // bound on |FP32 distance - exact distance| for any two nodes
 };
 
@@ -131,6 +132,7 @@ __global__ void k_grid_params(const double *partial, int nparts, int64_t N, doub
     for (int a = 0; a < DIM; ++a) amax = fmax(amax, fmax(fabs(lo[a]), fabs(hi[a])));
     for (int a = 0; a < 3; ++a) gp->lo32[a] = (float)gp->lo[a];
     gp->cell32 = (float)c;
+    gp->inv_cell32 = (float)(1.0 / c);
     // each coordinate rounds by <= u32*amax, the difference by <= 2*u32*amax,
     // the FP32 square, sum and root by a few u32 of the distance (<= 2*amax*sqrt(d))
     gp->delta32 = (float)(16.0 * (FLT_EPSILON * 0.5) * amax * sqrt((double)DIM)) + 1e-30f;
@@ -232,7 +234,7 @@ __global__ void k_scan_add(const int *tile_sum, const GridParams *gp, int *start
 template <int DIM>
 __global__ void k_scatter(const double *__restrict__ pts, int64_t N, const int *cell_of,
                           const int *rank, const int *start, double *spts, float *spts32,
-                          int *sidx) {
+                          int *sidx, float *pts32) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int d = start[cell_of[i]] + rank[i];
@@ -241,6 +243,7 @@ __global__ void k_scatter(const double *__restrict__ pts, int64_t N, const int *
             const double v = pts[i * DIM + a];
             spts[(int64_t)d * DIM + a] = v;
             spts32[(int64_t)d * DIM + a] = (float)v;
+            pts32[i * DIM + a] = (float)v;
         }
         sidx[d] = (int)i;
     }
@@ -291,22 +294,27 @@ struct TopList {
         d = __shfl_sync(kFull, dv, src);
         i = __shfl_sync(kFull, iv, src);
     }
-    // Insert a warp-uniform key known to be better than the worst.
+    // Insert a warp-uniform key known to be better than the worst.  With K
+    // <= 32 the second slots are never used (warp-uniform branch).
     __device__ void insert(u64 d, int idx) {
         const int lane = threadIdx.x & 31;
         const unsigned blo = __ballot_sync(kFull, key_lt(dlo, ilo, d, idx));
-        const unsigned bhi = __ballot_sync(kFull, key_lt(dhi, ihi, d, idx));
-        const int pos = __popc(blo) + __popc(bhi);
+        int pos = __popc(blo);
         const u64 pdlo = __shfl_up_sync(kFull, dlo, 1);
         const int pilo = __shfl_up_sync(kFull, ilo, 1);
-        u64 pdhi = __shfl_up_sync(kFull, dhi, 1);
-        int pihi = __shfl_up_sync(kFull, ihi, 1);
-        const u64 d31 = __shfl_sync(kFull, dlo, 31);
-        const int i31 = __shfl_sync(kFull, ilo, 31);
-        if (lane == 0) { pdhi = d31; pihi = i31; }
-        const int slo = lane, shi = lane + 32;
-        if (shi > pos) { dhi = pdhi; ihi = pihi; }
-        if (shi == pos) { dhi = d; ihi = idx; }
+        if (K > 32) {
+            const unsigned bhi = __ballot_sync(kFull, key_lt(dhi, ihi, d, idx));
+            pos += __popc(bhi);
+            u64 pdhi = __shfl_up_sync(kFull, dhi, 1);
+            int pihi = __shfl_up_sync(kFull, ihi, 1);
+            const u64 d31 = __shfl_sync(kFull, dlo, 31);
+            const int i31 = __shfl_sync(kFull, ilo, 31);
+            if (lane == 0) { pdhi = d31; pihi = i31; }
+            const int shi = lane + 32;
+            if (shi > pos) { dhi = pdhi; ihi = pihi; }
+            if (shi == pos) { dhi = d; ihi = idx; }
+        }
+        const int slo = lane;
         if (slo > pos) { dlo = pdlo; ilo = pilo; }
         if (slo == pos) { dlo = d; ilo = idx; }
     }
@@ -387,14 +395,30 @@ __device__ __forceinline__ void write_row(const TopList &tl, int64_t q, int n, i
 }
 
 // ---------------------------------------------------------- grid ring search
+// Candidates that pass the FP32 filter wait in a per-warp queue in shared
+// memory and get their exact FP64 keys 32 at a time, so FP64 instructions
+// (1/64 of the FP32 rate on this GPU, and issued for the whole warp however
+// few lanes need them) run on full batches; the queue is also flushed at the
+// end of every ring, before the stop test.  While candidates wait, the list's
+// worst key is older (larger) than it would be, which only lets more
+// candidates through the conservative tests; the final list is the same,
+// because the ranking is a total order and every candidate that can enter it
+// passes.
+constexpr int kQueue = 64;
+
 template <int DIM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__restrict__ start,
-           const double *__restrict__ spts, const float *__restrict__ spts32,
+k_knn_grid(const double *__restrict__ pts, const float *__restrict__ pts32, const GridParams *gp,
+           const int *__restrict__ start, const double *__restrict__ spts, const float *__restrict__ spts32,
            const int *__restrict__ sidx, int64_t q_begin, int64_t q_end, int n,
            int32_t *__restrict__ out, int32_t *status) {
+    __shared__ int s_sp[kWarpsPerBlock][kQueue];
+    __shared__ int s_idx[kWarpsPerBlock][kQueue];
     const GridParams g = *gp;
     const int lane = threadIdx.x & 31;
+    int *qsp = s_sp[threadIdx.x >> 5];
+    int *qidx = s_idx[threadIdx.x >> 5];
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float delta = g.delta32;
@@ -409,15 +433,55 @@ k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__re
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             c[a] = pts[q * DIM + a];
-            c32[a] = (float)c[a];
-            cq[a] = cell_coord<DIM>(c[a], a, g);
+            c32[a] = pts32[q * DIM + a];
+            // ring centre: the query's cell up to FP32 rounding (any cell is
+            // a valid centre: the rings, the pruning and the stop test use
+            // the query's own coordinates)
+            const int i = __float2int_rd((c32[a] - g.lo32[a]) * g.inv_cell32);
+            cq[a] = min(max(i, 0), g.dims[a] - 1);
         }
         TopList tl;
         tl.init(n - 1);
         u64 wd;
         int wi;
         tl.worst(wd, wi);
+        // FP32 upper bound of the worst kept squared distance, and the
+        // squared FP32 distance a candidate must not exceed to possibly beat
+        // it (sqrt(d2f) - delta <= sqrt(worst), with a relative margin)
+        float wf = 0.0f, thr = 0.0f;
+        auto bounds = [&]() {
+            wf = worst_f32(wd);
+            const float r = sqrtf(wf * 1.000001f) + delta;
+            thr = r * r * 1.00001f;
+        };
+        bounds();
         bool dup = false;
+        int qn = 0;
+        // exact keys of the first `cnt` queued candidates, insertion of those
+        // that beat the worst kept
+        auto flush = [&](int cnt) {
+            const bool v = lane < cnt;
+            const int sp = v ? qsp[lane] : 0;
+            const int idx = v ? qidx[lane] : -1;
+            u64 key = kInfBits;
+            if (v) {
+                const double d2 = dist2_rn<DIM>(spts + (int64_t)sp * DIM, c);
+                key = (u64)__double_as_longlong(d2);
+                if (d2 == 0.0) dup = true;
+            }
+            unsigned m = __ballot_sync(kFull, v && key_lt(key, idx, wd, wi));
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const u64 ck = __shfl_sync(kFull, key, src);
+                const int ci = __shfl_sync(kFull, idx, src);
+                if (key_lt(ck, ci, wd, wi)) {
+                    tl.insert(ck, ci);
+                    tl.worst(wd, wi);
+                }
+            }
+            bounds();
+        };
         for (int t = 0; t <= maxdim; ++t) {
             const int side = 2 * t + 1;
             int ncube = side;
@@ -447,7 +511,7 @@ k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__re
                         const float gap = fmaxf(0.0f, fmaxf(blo - c32[a], c32[a] - bhi));
                         md2 = fmaf(gap, gap, md2);
                     }
-                    if (inside && cheb == t && !(md2 * 0.99999f > worst_f32(wd))) {
+                    if (inside && cheb == t && !(md2 * 0.99999f > wf)) {
                         cstart = start[cid];
                         ccount = start[cid + 1] - cstart;
                     }
@@ -471,19 +535,45 @@ k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__re
                     const int os = __shfl_sync(kFull, cstart, owner);
                     const int oi = __shfl_sync(kFull, incl, owner);
                     const int oc = __shfl_sync(kFull, ccount, owner);
-                    bool valid = p < total;
+                    bool pass = false;
                     int sp = 0, idx = -1;
-                    float x32[DIM];
-                    if (valid) {
+                    if (p < total) {
                         sp = os + (p - (oi - oc));
                         idx = sidx[sp];
+                        float d2f = 0.0f;
 #pragma unroll
-                        for (int a = 0; a < DIM; ++a) x32[a] = spts32[(int64_t)sp * DIM + a];
-                        valid = idx != (int)q;
+                        for (int a = 0; a < DIM; ++a) {
+                            const float tt = spts32[(int64_t)sp * DIM + a] - c32[a];
+                            d2f = fmaf(tt, tt, d2f);
+                        }
+                        pass = idx != (int)q && d2f <= thr;
                     }
-                    consider<DIM>(tl, valid, x32, c32, spts + (int64_t)sp * DIM, c, idx, delta, wd,
-                                  wi, dup);
+                    const unsigned pm = __ballot_sync(kFull, pass);
+                    if (pm) {
+                        const int at = qn + __popc(pm & lt_mask);
+                        if (pass) {
+                            qsp[at] = sp;
+                            qidx[at] = idx;
+                        }
+                        qn += __popc(pm);
+                        __syncwarp();
+                        if (qn >= 32) {
+                            flush(32);
+                            __syncwarp();
+                            if (lane < qn - 32) {
+                                qsp[lane] = qsp[32 + lane];
+                                qidx[lane] = qidx[32 + lane];
+                            }
+                            qn -= 32;
+                            __syncwarp();
+                        }
+                    }
                 }
+            }
+            if (qn > 0) {
+                flush(qn);
+                qn = 0;
+                __syncwarp();
             }
             // stop once every unvisited cell is provably farther than the worst kept
             bool covers = true;
@@ -497,7 +587,7 @@ k_knn_grid(const double *__restrict__ pts, const GridParams *gp, const int *__re
             }
             if (covers) break;
             bd = fmaxf(bd - slack, 0.0f);
-            if (bd * bd * 0.99999f > worst_f32(wd)) break;
+            if (bd * bd * 0.99999f > wf) break;
         }
         dup = __any_sync(kFull, dup);
         write_row(tl, q, n, out + (q - q_begin) * n, status, dup);
@@ -591,6 +681,7 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     const size_t o_spts = wc.take<double>((size_t)N * DIM);
     const size_t o_spts32 = wc.take<float>((size_t)N * DIM);
     const size_t o_sidx = wc.take<int>((size_t)N);
+    const size_t o_pts32 = wc.take<float>((size_t)N * DIM);
     const size_t o_tiles = wc.take<int>((size_t)ntiles + 1);
     char *ws = mm_workspace(ctx, wc.off);
     if (!ws) return mm_fail(ctx, MM_ENOMEM, "knn workspace of %zu bytes", wc.off);
@@ -601,6 +692,7 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     double *spts = (double *)(ws + o_spts);
     float *spts32 = (float *)(ws + o_spts32);
     int *sidx = (int *)(ws + o_sidx), *tiles = (int *)(ws + o_tiles);
+    float *pts32 = (float *)(ws + o_pts32);
     k_bbox_partial<DIM><<<bb_blocks, 256, 0, st>>>(d_pts, N, part);
     k_grid_params<DIM><<<1, 32, 0, st>>>(part, bb_blocks, N, ppc, cap, gp);
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(cap + 1), st));
@@ -608,15 +700,15 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count, gp, start, tiles);
     k_scan_sums<<<1, kScanThreads, 0, st>>>(tiles, ntiles, gp, start);
     k_scan_add<<<ntiles, kScanThreads, 0, st>>>(tiles, gp, start);
-    k_scatter<DIM><<<eb, 256, 0, st>>>(d_pts, N, cellof, rank, start, spts, spts32, sidx);
+    k_scatter<DIM><<<eb, 256, 0, st>>>(d_pts, N, cellof, rank, start, spts, spts32, sidx, pts32);
     MM_LAUNCH_CHECK(ctx);
     for (int r = 0; r < nranges; ++r) {
         const mm_knn_range &R = ranges[r];
         if (R.q_end <= R.q_begin) continue;
         const int64_t warps = R.q_end - R.q_begin;
         const int blocks = (int)std::min<int64_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, qblocks);
-        k_knn_grid<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, gp, start, spts, spts32, sidx,
-                                                                R.q_begin, R.q_end, R.n, R.d_idx,
+        k_knn_grid<DIM><<<blocks, kWarpsPerBlock * 32, 0, st>>>(d_pts, pts32, gp, start, spts, spts32,
+                                                                sidx, R.q_begin, R.q_end, R.n, R.d_idx,
                                                                 d_status);
         MM_LAUNCH_CHECK(ctx);
     }
