@@ -320,6 +320,38 @@ struct TopList {
     }
 };
 
+// One compare-exchange stage over the warp for sorted order of (key, index)
+// pairs: lane and lane ^ j exchange so that the lane with the lower position
+// in the pair's direction keeps the smaller pair (`up`: this lane's pair
+// sorts ascending).
+__device__ __forceinline__ void cmpx(u64 &k, int &i, int j, bool up) {
+    const int lane = threadIdx.x & 31;
+    const u64 ok = __shfl_xor_sync(kFull, k, j);
+    const int oi = __shfl_xor_sync(kFull, i, j);
+    const bool lower = (lane & j) == 0;
+    const bool other_smaller = key_lt(ok, oi, k, i);
+    // keep the smaller one if (lower == up), else the larger one
+    if ((lower == up) == other_smaller) { k = ok; i = oi; }
+}
+
+// Merge of up to 32 new pairs (one per lane, +inf for none) into a list of
+// K <= 32 slots held one per lane in ascending order: bitonic sort of the new
+// pairs, the elementwise smaller of the list and the reversed new pairs (the
+// 32 smallest of both, as a bitonic sequence), bitonic merge.  ~21 exchange
+// stages, whatever the number of new pairs.
+__device__ __forceinline__ void merge_batch(TopList &tl, u64 k, int i) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 2; w <= 32; w <<= 1)
+#pragma unroll
+        for (int j = w >> 1; j; j >>= 1) cmpx(k, i, j, (lane & w) == 0 || w == 32);
+    const u64 rk = __shfl_sync(kFull, k, 31 - lane);
+    const int ri = __shfl_sync(kFull, i, 31 - lane);
+    if (key_lt(rk, ri, tl.dlo, tl.ilo)) { tl.dlo = rk; tl.ilo = ri; }
+#pragma unroll
+    for (int j = 16; j; j >>= 1) cmpx(tl.dlo, tl.ilo, j, true);
+}
+
 template <int DIM>
 __device__ __forceinline__ double dist2_rn(const double *p, const double *c) {
     double t = __dsub_rn(p[0], c[0]);
@@ -469,7 +501,14 @@ k_knn_grid(const double *__restrict__ pts, const float *__restrict__ pts32, cons
                 key = (u64)__double_as_longlong(d2);
                 if (d2 == 0.0) dup = true;
             }
-            unsigned m = __ballot_sync(kFull, v && key_lt(key, idx, wd, wi));
+            const bool better = v && key_lt(key, idx, wd, wi);
+            unsigned m = __ballot_sync(kFull, better);
+            if (tl.K <= 32 && __popc(m) >= 6) {
+                // many new entries: one bitonic merge instead of one insertion each
+                merge_batch(tl, better ? key : kInfBits, better ? idx : 0x7fffffff);
+                tl.worst(wd, wi);
+                m = 0;
+            }
             while (m) {
                 const int src = __ffs(m) - 1;
                 m &= m - 1;
