@@ -84,19 +84,33 @@ __global__ void k_bbox_partial(const double *__restrict__ pts, int64_t N, double
     }
 }
 
-// One thread: reduce the block partials, choose the cell edge so a cell holds
-// about `ppc` nodes on average, cap the cell count at `cap`.
+// One block: reduce the block partials (every thread a stride of them, then
+// the warps, then the first warp), then one thread chooses the cell edge so a
+// cell holds about `ppc` nodes on average and caps the cell count at `cap`.
 template <int DIM>
 __global__ void k_grid_params(const double *partial, int nparts, int64_t N, double ppc,
                               int64_t cap, GridParams *gp) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double s_lo[DIM][32], s_hi[DIM][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double lo[DIM], hi[DIM], ext[DIM], emax = 0;
+#pragma unroll
     for (int a = 0; a < DIM; ++a) {
         lo[a] = DBL_MAX; hi[a] = -DBL_MAX;
-        for (int j = 0; j < nparts; ++j) {
+        for (int j = threadIdx.x; j < nparts; j += blockDim.x) {
             lo[a] = fmin(lo[a], partial[j * 2 * DIM + a]);
             hi[a] = fmax(hi[a], partial[j * 2 * DIM + DIM + a]);
         }
+        for (int o = 16; o; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(kFull, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(kFull, hi[a], o));
+        }
+        if (lane == 0) { s_lo[a][w] = lo[a]; s_hi[a][w] = hi[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int a = 0; a < DIM; ++a) {
+        lo[a] = s_lo[a][0]; hi[a] = s_hi[a][0];
+        for (int j = 1; j < nw; ++j) { lo[a] = fmin(lo[a], s_lo[a][j]); hi[a] = fmax(hi[a], s_hi[a][j]); }
         ext[a] = hi[a] - lo[a];
         emax = fmax(emax, ext[a]);
     }
@@ -438,8 +452,9 @@ __device__ __forceinline__ void write_row(const TopList &tl, int64_t q, int n, i
 // passes.
 constexpr int kQueue = 64;
 
+// (64 registers, no spills: four blocks of eight warps per SM)
 template <int DIM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 k_knn_grid(const double *__restrict__ pts, const float *__restrict__ pts32, const GridParams *gp,
            const int *__restrict__ start, const double *__restrict__ spts, const float *__restrict__ spts32,
            const int *__restrict__ sidx, int64_t q_begin, int64_t q_end, int n,
@@ -733,7 +748,7 @@ int knn_impl(mm_ctx *ctx, int64_t N, const double *d_pts, int nranges, const mm_
     int *sidx = (int *)(ws + o_sidx), *tiles = (int *)(ws + o_tiles);
     float *pts32 = (float *)(ws + o_pts32);
     k_bbox_partial<DIM><<<bb_blocks, 256, 0, st>>>(d_pts, N, part);
-    k_grid_params<DIM><<<1, 32, 0, st>>>(part, bb_blocks, N, ppc, cap, gp);
+    k_grid_params<DIM><<<1, 256, 0, st>>>(part, bb_blocks, N, ppc, cap, gp);
     MM_CUDA_CHECK(ctx, cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(cap + 1), st));
     k_cell_count<DIM><<<eb, 256, 0, st>>>(d_pts, N, gp, cellof, rank, count);
     k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count, gp, start, tiles);
