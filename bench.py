@@ -665,6 +665,9 @@ def run_disk(args, rk):
                  "achieved": spmv_bytes / (apply_ms * 1e-3) / 1e9, "unit": "GB/s",
                  "peak": hbm, "frac": (spmv_bytes / (apply_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                  "bytes": spmv_bytes, "ms": apply_ms,
+                 "fp64_pipe_frac": 3 * 2.0 * pipe.nnz / (apply_ms * 1e-3) / fp64_peak,
+                 "note": "one FP64 multiply-add per nonzero: fp64_pipe_frac is their rate against the measured "
+                         "FP64 peak; on GB300 the FP64 pipe co-bounds this kernel with HBM",
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     # the method's flops delivered per second by the chosen form, against FP64
     fp64_equiv = {"tflops": f64_plain / (dom_ms * 1e-3) / 1e12,
@@ -677,8 +680,9 @@ def run_disk(args, rk):
                 "achieved": knn_bytes / (knn_ms * 1e-3) / 1e9, "unit": "GB/s", "peak": hbm,
                 "frac": (knn_bytes / (knn_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                 "bytes": knn_bytes, "ms": knn_ms, "nodes_per_s": ns.N / (knn_ms * 1e-3),
-                "note": "HBM reference of the survey; the ring search is bound by its integer and "
-                        "FP32 candidate tests, not by HBM",
+                "note": "HBM reference of the survey; the ring search is bound by integer/ALU issue "
+                        "(keys compared as integers), with the exact FP64 keys on full batches keeping "
+                        "the FP64 pipe about half busy; not by HBM",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": rk.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
