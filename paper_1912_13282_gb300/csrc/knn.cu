@@ -22,7 +22,8 @@
 //    and stops once the ring boundary is farther than the n-th best.
 //  * brute: every node is a candidate (for small N).
 // The top n-1 list lives in registers across the warp (two slots per lane,
-// n <= 65) and is kept sorted by warp-wide insertion.
+// n <= 65) and is kept sorted by warp-wide insertion, or by a bitonic merge
+// when a batch brings many new entries.
 #include <float.h>
 #include <math.h>
 
@@ -348,6 +349,20 @@ __device__ __forceinline__ void cmpx(u64 &k, int &i, int j, bool up) {
     if ((lower == up) == other_smaller) { k = ok; i = oi; }
 }
 
+// Bitonic sort of 32 pairs (one per lane) into ascending lane order.
+__device__ __forceinline__ void sort32(u64 &k, int &i) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 2; w <= 32; w <<= 1)
+#pragma unroll
+        for (int j = w >> 1; j; j >>= 1) cmpx(k, i, j, (lane & w) == 0 || w == 32);
+}
+// A bitonic sequence of 32 pairs into ascending lane order.
+__device__ __forceinline__ void bitonic32(u64 &k, int &i) {
+#pragma unroll
+    for (int j = 16; j; j >>= 1) cmpx(k, i, j, true);
+}
+
 // Merge of up to 32 new pairs (one per lane, +inf for none) into a list of
 // K <= 32 slots held one per lane in ascending order: bitonic sort of the new
 // pairs, the elementwise smaller of the list and the reversed new pairs (the
@@ -355,15 +370,37 @@ __device__ __forceinline__ void cmpx(u64 &k, int &i, int j, bool up) {
 // stages, whatever the number of new pairs.
 __device__ __forceinline__ void merge_batch(TopList &tl, u64 k, int i) {
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int w = 2; w <= 32; w <<= 1)
-#pragma unroll
-        for (int j = w >> 1; j; j >>= 1) cmpx(k, i, j, (lane & w) == 0 || w == 32);
+    sort32(k, i);
     const u64 rk = __shfl_sync(kFull, k, 31 - lane);
     const int ri = __shfl_sync(kFull, i, 31 - lane);
     if (key_lt(rk, ri, tl.dlo, tl.ilo)) { tl.dlo = rk; tl.ilo = ri; }
-#pragma unroll
-    for (int j = 16; j; j >>= 1) cmpx(tl.dlo, tl.ilo, j, true);
+    bitonic32(tl.dlo, tl.ilo);
+}
+
+// The same for a list of 33 <= K <= 64 slots (lo: slots 0..31, hi: 32..63).
+// With the new pairs B sorted and reversed, min(lo, B) are the 32 smallest of
+// lo and B, all no larger than any hi slot (lo alone has 32 such), so they
+// are the new lo; max(lo, B), the 32 largest of lo and B, merge with hi the
+// same way for the new hi.  ~32 exchange stages.
+__device__ __forceinline__ void merge_batch2(TopList &tl, u64 k, int i) {
+    const int lane = threadIdx.x & 31;
+    sort32(k, i);
+    const u64 rk = __shfl_sync(kFull, k, 31 - lane);
+    const int ri = __shfl_sync(kFull, i, 31 - lane);
+    u64 yk = rk;
+    int yi = ri;
+    if (key_lt(rk, ri, tl.dlo, tl.ilo)) {
+        yk = tl.dlo;
+        yi = tl.ilo;
+        tl.dlo = rk;
+        tl.ilo = ri;
+    }
+    bitonic32(tl.dlo, tl.ilo);
+    bitonic32(yk, yi);
+    const u64 zk = __shfl_sync(kFull, yk, 31 - lane);
+    const int zi = __shfl_sync(kFull, yi, 31 - lane);
+    if (key_lt(zk, zi, tl.dhi, tl.ihi)) { tl.dhi = zk; tl.ihi = zi; }
+    bitonic32(tl.dhi, tl.ihi);
 }
 
 template <int DIM>
@@ -452,9 +489,9 @@ __device__ __forceinline__ void write_row(const TopList &tl, int64_t q, int n, i
 // passes.
 constexpr int kQueue = 64;
 
-// (64 registers, no spills: four blocks of eight warps per SM)
+// (2D: 64 registers, no spills, four blocks of eight warps per SM; 3D: three)
 template <int DIM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, DIM == 2 ? 4 : 3)
 k_knn_grid(const double *__restrict__ pts, const float *__restrict__ pts32, const GridParams *gp,
            const int *__restrict__ start, const double *__restrict__ spts, const float *__restrict__ spts32,
            const int *__restrict__ sidx, int64_t q_begin, int64_t q_end, int n,
@@ -521,6 +558,10 @@ k_knn_grid(const double *__restrict__ pts, const float *__restrict__ pts32, cons
             if (tl.K <= 32 && __popc(m) >= 6) {
                 // many new entries: one bitonic merge instead of one insertion each
                 merge_batch(tl, better ? key : kInfBits, better ? idx : 0x7fffffff);
+                tl.worst(wd, wi);
+                m = 0;
+            } else if (tl.K > 32 && __popc(m) >= 8) {
+                merge_batch2(tl, better ? key : kInfBits, better ? idx : 0x7fffffff);
                 tl.worst(wd, wi);
                 m = 0;
             }
