@@ -704,6 +704,10 @@ def run_disk(args, rk):
                                "note": "same form, refinement residuals in native FP64"},
             "fp64_equivalent": fp64_equiv,
             "speedup_vs_fp64_plain": ms64 / ms, "weights_ms": float(np.mean(wts)),
+            "weights_only": {"value": n_all / (float(np.mean(wts)) * 1e-3), "unit": "nodes/s",
+                             "fp64_plain": n_all / (float(np.mean(w64)) * 1e-3),
+                             "note": "both classes' weights without the kNN and the operator "
+                                     "applications (the headline value is kNN + weights + applications)"},
             "fallback_fraction": fallback, "roofline": roof, "roofline_spmv": spmv_roof,
             "roofline_knn": knn_roof,
             "roofline_combine": comb_roof,
