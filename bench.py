@@ -534,6 +534,49 @@ def cpu_baseline_disk(ns, rp, col_h, seconds=15.0, seed=0):
                               "knn_s_per_node": t_knn1, "weights_s_per_node": t_w1}}
 
 
+def cpu_baseline_classes(ns, rp, col_h, spans, seconds=15.0, seed=0):
+    """The oracle timed on the host cores on a bounded sample of a workload
+    with several stencil classes (spans: (row_begin, row_end, n, k, m, ops)): per class,
+    brute-force kNN of some of its queries and weights of some of its rows,
+    weighted by the class's share of the nodes; all cores, and one thread on
+    a smaller sample.  nodes/s of kNN + weights."""
+    from oracle import oracle as O
+    threads = O.nthreads_default()
+    rng = np.random.default_rng(seed)
+    shares = [(e - b) / ns.N for b, e, *_ in spans]
+
+    def timed(nthreads, queries_total, rows_total):
+        t_knn = t_w = 0.0
+        q_used = r_used = 0
+        for (b, e, n, k, m, ops), share in zip(spans, shares):
+            nq = max(1, min(e - b, int(queries_total * share)))
+            q = rng.choice(np.arange(b, e), nq, replace=False)
+            t0 = time.perf_counter()
+            O.knn(ns.pts, n, queries=q, nthreads=nthreads)
+            t_knn += (time.perf_counter() - t0) / nq * share
+            nr = max(1, min(e - b, int(rows_total * share)))
+            rows = np.sort(rng.choice(np.arange(b, e), nr, replace=False))
+            t0 = time.perf_counter()
+            oracle_rows(ns, rp, col_h, rows, k, m, ops, nthreads=nthreads)
+            t_w += (time.perf_counter() - t0) / nr * share
+            q_used += nq
+            r_used += nr
+        return t_knn, t_w, q_used, r_used
+
+    # size the all-core sample from a short probe so it takes about `seconds`
+    tk, tw, _, _ = timed(threads, 64, 256)
+    scale = max(1.0, seconds / max((tk * 64 + tw * 256), 1e-9))
+    t_knn, t_w, nq, nr = timed(threads, int(min(20000, 64 * scale)), int(min(20000, 256 * scale)))
+    t_knn1, t_w1, nq1, nr1 = timed(1, 32, 256)
+    return {"value": 1.0 / (t_knn + t_w), "unit": "nodes/s", "cores": threads, "kind": "oracle",
+            "sample": f"{nq} brute-force kNN queries over all {ns.N} nodes + {nr} weight rows "
+                      f"(classes in proportion to their nodes), all host cores",
+            "knn_s_per_node": t_knn, "weights_s_per_node": t_w,
+            "single_thread": {"value": 1.0 / (t_knn1 + t_w1), "unit": "nodes/s", "cores": 1,
+                              "sample": f"{nq1} kNN queries + {nr1} weight rows, one thread",
+                              "knn_s_per_node": t_knn1, "weights_s_per_node": t_w1}}
+
+
 def run_disk(args, rk):
     import torch
     import paper_1912_13282_gb300 as P
@@ -818,6 +861,9 @@ def run_ball(args, rk):
             "fallback_fraction": float((st == P.binding.ST_FALLBACK).mean()),
             "autotuned": tuned, "clocks": clk,
             "gpu_launches": (11 + 2 + 4) * args.steps}
+    if rk.rank == 0 and rk.world == 1 and not args.no_cpu_baseline:
+        spans = [(ns.classes[c][0], ns.classes[c][1], n, k, m, ops) for c, n, k, m, ops in BALL["classes"]]
+        line["cpu_baseline"] = cpu_baseline_classes(ns, rp, col.cpu().numpy(), spans)
     ctx.close()
     return line
 
@@ -1306,6 +1352,8 @@ def run_square(args, rk):
                        "note": "10^4 nodes: the step is launch-bound (16 launches)"},
             "fp64_plain": res["fp64"], "fp32_ir": res["fp32_ir"], "error": out_err, "poisson": poisson,
             "clocks": clk, "gpu_launches": 16 * args.steps * 2}
+    if rk.rank == 0 and rk.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_classes(ns, rp_h, col.cpu().numpy(), [(0, N, n, k, m, ops)])
     ctx.close()
     return line
 
