@@ -112,6 +112,36 @@ __device__ __forceinline__ double phs(double r2, int k) {
     return p;
 }
 
+// 1/d from an FP32 seed refined by one Halley step.  The seed is the FP32
+// reciprocal of d's sign, exponent and leading 23 mantissa bits, moved
+// between the formats by integer operations on the bit patterns (relative
+// error below 2^-22, no FP64 instruction: GB300's FP64 pipe issues at ~1/64
+// of the FP32 rate and charges a conversion like an FMA).  With e = 1 - d y,
+// 1/d = y (1 + e + e^2 + ...), so y + y (e + e^2) leaves a relative error of
+// ~e^3 < 2^-66 before its final rounding: three FP64 FMAs.  An exponent
+// outside +-120 takes the IEEE division.
+__device__ __forceinline__ double recip_nr(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int ex = (int)((b >> 52) & 0x7FFull) - 1023;
+    if (ex < -120 || ex > 120) return 1.0 / d;
+    const unsigned fb = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)(ex + 127) << 23) |
+                        (unsigned)((b >> 29) & 0x7FFFFFull);
+    const unsigned yb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+    const int ey = (int)((yb >> 23) & 0xFFu) - 127;
+    const double y = __longlong_as_double((long long)(((unsigned long long)(yb & 0x80000000u) << 32) |
+                                                      ((unsigned long long)(ey + 1023) << 52) |
+                                                      ((unsigned long long)(yb & 0x7FFFFFu) << 29)));
+    const double e = fma(-d, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
+// |v| > tiny (tiny >= 0) on the bit patterns: integer compares instead of an
+// FP64 one; NaN fails, as `!(fabs(v) > tiny)` would.
+__device__ __forceinline__ bool abs_gt(double v, double tiny) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    return a > (unsigned long long)__double_as_longlong(tiny) && a <= 0x7FF0000000000000ull;
+}
+
 // Per-row prologue: validates the stencil, loads and scales offsets into
 // xi [n x DIM] (shared), returns n and s (0 if the row is bad).
 template <int DIM>
@@ -125,7 +155,9 @@ __device__ bool load_stencil(const WParams &P, int64_t row, int &n, int64_t &rb,
     double c[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) c[a] = P.pts[row * DIM + a];
-    double r2max = 0.0;
+    // the largest r^2 kept as the largest bit pattern (r^2 >= 0): integer
+    // compares and shuffles instead of FP64 ones
+    unsigned long long r2bits = 0ull;
     for (int j = lane; j < n; j += 32) {
         int g = P.col[rb + j];
         if (g < 0 || g >= P.N || (j == 0 && g != row)) { bad = true; continue; }
@@ -136,13 +168,15 @@ __device__ bool load_stencil(const WParams &P, int64_t row, int &n, int64_t &rb,
             xi[j * DIM + a] = d;
             r2 = fma(d, d, r2);
         }
-        r2max = fmax(r2max, r2);
+        r2bits = max(r2bits, (unsigned long long)__double_as_longlong(r2));
     }
     bad = __any_sync(kFull, bad);
-    r2max = warp_max(r2max);
-    if (bad || !(r2max > 0.0)) { s = 0.0; return false; }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) r2bits = max(r2bits, __shfl_xor_sync(kFull, r2bits, o));
+    const double r2max = __longlong_as_double((long long)r2bits);
+    if (bad || !(r2bits > 0ull && r2bits < 0x7FF0000000000000ull)) { s = 0.0; return false; }
     s = sqrt(r2max);
-    double inv = 1.0 / s;
+    const double inv = recip_nr(s);
     __syncwarp();
     for (int j = lane; j < n * DIM; j += 32) xi[j] *= inv;
     __syncwarp();
@@ -172,22 +206,28 @@ __device__ double assemble_fp64(const WParams &P, int64_t row, int n, const doub
     // max |K| kept as the largest bit pattern of the (non-negative) |values|:
     // integer compares instead of FP64 ones
     unsigned long long amax_bits = 0ull;
-    // A: unordered pairs (r, (r + d) mod n), d = 1 .. n/2, each once
-    for (int d = 1; d <= n / 2; ++d) {
-        int cnt = (2 * d == n) ? n / 2 : n;
-        for (int r = lane; r < cnt; r += 32) {
-            int c = r + d;
-            if (c >= n) c -= n;
-            double r2 = 0.0;
+    // A: the n (n - 1) / 2 unordered pairs (r, (r + d) mod n), d = 1 .. n/2
+    // (r < n/2 for d = n/2), numbered t = (d - 1) n + r and dealt to the
+    // lanes in turn, so every lane has a pair in all but the last round
+    const int npairs = n * (n - 1) / 2;
+    int dd = 1 + lane / max(n, 1), rr = lane % max(n, 1);
+    for (int t = lane; t < npairs; t += 32) {
+        int c = rr + dd;
+        if (c >= n) c -= n;
+        double r2 = 0.0;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                double t = xi[r * DIM + a] - xi[c * DIM + a];
-                r2 = fma(t, t, r2);
-            }
-            double v = phs(r2, k);
-            K[r * pitch + c] = v;
-            K[c * pitch + r] = v;
-            amax_bits = max(amax_bits, (unsigned long long)__double_as_longlong(v));
+        for (int a = 0; a < DIM; ++a) {
+            double tt = xi[rr * DIM + a] - xi[c * DIM + a];
+            r2 = fma(tt, tt, r2);
+        }
+        double v = phs(r2, k);
+        K[rr * pitch + c] = v;
+        K[c * pitch + rr] = v;
+        amax_bits = max(amax_bits, (unsigned long long)__double_as_longlong(v));
+        rr += 32;
+        while (rr >= n) {
+            rr -= n;
+            ++dd;
         }
     }
     for (int r = lane; r < n; r += 32) K[r * pitch + r] = 0.0;
@@ -271,7 +311,7 @@ template <class T>
 __device__ void store_weights(const WParams &P, int64_t rb, int n, double s, const T *X, int xp,
                               int col0) {
     const int lane = threadIdx.x & 31;
-    double inv_s = 1.0 / s;
+    const double inv_s = recip_nr(s);
     for (int cI = 0; cI < P.R; ++cI) {
         double sc = op_order(P.opcode[cI]) == 2 ? inv_s * inv_s : inv_s;
         double *out = P.vals[cI] + rb;
@@ -290,20 +330,6 @@ __device__ __forceinline__ unsigned pivot_key64(double v, int r) {
     return (hi & 0xFFFFFF80u) | (unsigned)(127 - r);
 }
 
-// 1/d by Newton-Raphson iteration for the reciprocal, y <- y + y (1 - d y),
-// from the FP32 reciprocal of d: each step squares the relative error
-// (2^-23 -> 2^-46 -> below FP64 rounding), i.e. 4 FP64 FMAs instead of a
-// full IEEE division.  Pivots outside the FP32 normal range take the division.
-__device__ __forceinline__ double recip_nr(double d) {
-    const double a = fabs(d);
-    if (!(a > 1e-30 && a < 1e30)) return 1.0 / d;
-    double y = (double)__frcp_rn((float)d);
-    double e = fma(-d, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-d, y, 1.0);
-    return fma(y, e, y);
-}
-
 // Gaussian elimination with row partial pivoting on [K | B] (M rows, M+R
 // columns), then back substitution; solution overwrites columns M..M+R-1.
 // Returns false if a pivot is not larger than M * u * amax.
@@ -317,7 +343,7 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
         for (int r = kk + lane; r < M; r += 32) key = max(key, pivot_key64(K[r * pitch + kk], r));
         const int prow = 127 - (int)(__reduce_max_sync(kFull, key) & 0x7Fu);
         const double piv = K[prow * pitch + kk];
-        if (!(fabs(piv) > tiny)) return false;
+        if (!abs_gt(piv, tiny)) return false;
         if (prow != kk) {
             for (int c = kk + lane; c < W_all; c += 32) {
                 double t = K[kk * pitch + c];
@@ -1486,7 +1512,7 @@ __device__ __noinline__ bool mixed_row(const WParams &P, int64_t row, char *base
         return true;
     }
     // unscaled store
-    const double inv_s = 1.0 / s;
+    const double inv_s = recip_nr(s);
     for (int cI = 0; cI < P.R; ++cI) {
         const double sc = op_order(P.opcode[cI]) == 2 ? inv_s * inv_s : inv_s;
         double *out = P.vals[cI] + rb;
