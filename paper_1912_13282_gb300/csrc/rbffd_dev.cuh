@@ -332,9 +332,13 @@ __device__ __forceinline__ unsigned pivot_key64(double v, int r) {
 
 // Gaussian elimination with row partial pivoting on [K | B] (M rows, M+R
 // columns), then back substitution; solution overwrites columns M..M+R-1.
+// Each pivot row is scaled by 1/pivot as it is swapped into place (one pass
+// over its W entries), so the elimination uses the rows' own column entries
+// as multipliers and the back substitution needs no division or scaling:
+// fewer partially filled FP64 warp instructions than a multiplier column
+// and a per-row scaling of the solution.
 // Returns false if a pivot is not larger than M * u * amax.
-__device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, double *invp,
-                              double *mul) {
+__device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax) {
     const int lane = threadIdx.x & 31;
     const double tiny = (double)M * (DBL_EPSILON * 0.5) * amax;
     const int W_all = M + R;
@@ -344,17 +348,15 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
         const int prow = 127 - (int)(__reduce_max_sync(kFull, key) & 0x7Fu);
         const double piv = K[prow * pitch + kk];
         if (!abs_gt(piv, tiny)) return false;
-        if (prow != kk) {
-            for (int c = kk + lane; c < W_all; c += 32) {
-                double t = K[kk * pitch + c];
-                K[kk * pitch + c] = K[prow * pitch + c];
-                K[prow * pitch + c] = t;
-            }
-            __syncwarp();
-        }
         const double ip = recip_nr(piv);
-        if (lane == 0) invp[kk] = ip;
-        for (int r = kk + 1 + lane; r < M; r += 32) mul[r] = K[r * pitch + kk] * ip;
+        // row kk <- row prow / pivot (columns kk+1 ..); row prow <- row kk
+        // (its column kk is the multiplier the elimination reads)
+        if (lane == 0 && prow != kk) K[prow * pitch + kk] = K[kk * pitch + kk];
+        for (int c = kk + 1 + lane; c < W_all; c += 32) {
+            const double a = K[prow * pitch + c];
+            if (prow != kk) K[prow * pitch + c] = K[kk * pitch + c];
+            K[kk * pitch + c] = a * ip;
+        }
         __syncwarp();
         const int W = W_all - kk - 1, H = M - kk - 1;
         if (H > 0) {
@@ -363,7 +365,7 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
             const double *Uk = K + kk * pitch + kk + 1;
             for (; r < H;) {
                 double *dst = K + (kk + 1 + r) * pitch + kk + 1 + c;
-                *dst = fma(-mul[kk + 1 + r], Uk[c], *dst);
+                *dst = fma(-K[(kk + 1 + r) * pitch + kk], Uk[c], *dst);
                 c += r32;
                 r += q32;
                 if (c >= W) { c -= W; ++r; }
@@ -371,10 +373,8 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
         }
         __syncwarp();
     }
-    // back substitution, R columns at once
+    // back substitution, R columns at once (unit diagonal)
     for (int kk = M - 1; kk >= 0; --kk) {
-        if (lane < R) K[kk * pitch + M + lane] *= invp[kk];
-        __syncwarp();
         for (int e = lane; e < kk * R; e += 32) {
             int r = e / R, c = e - r * R;
             K[r * pitch + M + c] = fma(-K[r * pitch + kk], K[kk * pitch + M + c], K[r * pitch + M + c]);
@@ -386,7 +386,7 @@ __device__ bool lu_solve_fp64(double *K, int pitch, int M, int R, double amax, d
 
 // Per-warp shared-memory layout of the FP64 kernel (in doubles).
 __host__ __device__ inline size_t fp64_warp_doubles(int M_max, int pitch64, int n_max, int dim) {
-    return (size_t)M_max * pitch64 + 2 * (size_t)M_max + (size_t)n_max * dim + 2;
+    return (size_t)M_max * pitch64 + (size_t)n_max * dim + 2;
 }
 
 // One stencil (row) with the FP64 solver; `base` is the warp's shared memory.
@@ -395,9 +395,7 @@ template <int DIM>
 __device__ __noinline__ void fp64_row(const WParams &P, int64_t row, double *base, bool from_fallback) {
     const int lane = threadIdx.x & 31;
     double *K = base;
-    double *invp = K + (size_t)P.M_max * P.pitch64;
-    double *mul = invp + P.M_max;
-    double *xi = mul + P.M_max;
+    double *xi = K + (size_t)P.M_max * P.pitch64;
     int n;
     int64_t rb;
     double s;
@@ -408,7 +406,7 @@ __device__ __noinline__ void fp64_row(const WParams &P, int64_t row, double *bas
     }
     const int M = n + P.l;
     const double amax = assemble_fp64<DIM>(P, row, n, xi, K, P.pitch64, n);
-    if (!lu_solve_fp64(K, P.pitch64, M, P.R, amax, invp, mul)) {
+    if (!lu_solve_fp64(K, P.pitch64, M, P.R, amax)) {
         reject_row(P, row, rb, n, MM_ST_SINGULAR);
         __syncwarp();
         return;
