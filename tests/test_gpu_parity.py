@@ -396,6 +396,35 @@ def test_spmv_and_diffuse_match_oracle(P, ctx, oracle, weight_inputs):
     assert np.abs(u_d.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("max_len", [60, 200])
+def test_spmv_ragged_rows_match_oracle(P, ctx, oracle, max_len):
+    """Random CSR rows of 0..max_len entries (mean ~30 or ~100, so both the
+    2-lane and the 4-lane row groups run), covering every split of a lane's
+    entries into batches of 8, 4, 2 and 1 and empty rows; y = alpha L u + beta
+    y and y = L u within the rounding bound of the oracle's sum."""
+    rng = np.random.default_rng(17 + max_len)
+    nrows, ncols = 20011, 5003
+    lens = rng.integers(0, max_len + 1, nrows)
+    lens[::97] = 0
+    rp = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = rng.integers(0, ncols, rp[-1]).astype(np.int32)
+    vals = rng.standard_normal(rp[-1])
+    u = rng.standard_normal(ncols)
+    y0 = rng.standard_normal(nrows)
+    absw = oracle.spmv(rp, col, np.abs(vals), np.abs(u))
+    for alpha, beta in ((1.0, 0.0), (-0.6, 2.5)):
+        y_d = dev(y0)
+        ctx.apply_operator(dev(rp), dev(col), dev(vals), dev(u), y_d, alpha=alpha, beta=beta)
+        torch.cuda.synchronize()
+        y = y_d.cpu().numpy()
+        ref = oracle.spmv(rp, col, vals, u, alpha=alpha, beta=beta, y=y0.copy())
+        bound = 2 * (lens + 2) * U64 * (abs(alpha) * absw + abs(beta) * np.abs(y0))
+        assert (np.abs(y - ref) <= bound).all(), (alpha, beta, np.abs(y - ref).max())
+        if beta == 0.0:
+            assert (y[lens == 0] == 0.0).all()
+
+
 def test_full_size_disk_sampled(P, ctx, oracle):
     """The 1,000,000-node disk-with-holes workload in the launch
     configuration the benchmark times: grid kNN + FP32/FP64-refined weights;
