@@ -73,7 +73,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="disk", choices=["disk", "ball", "batch", "surrogate", "wls", "poisson",
-                                                          "square"])
+                                                          "square", "balanced", "convdiff"])
     ap.add_argument("--n-target", type=int, default=None, help="override the node count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -1484,6 +1484,176 @@ def run_poisson(args, rk):
     return line
 
 
+# ------------------------------------------------------- balanced stencils
+BALANCED = {"workload": "disk minus 5 holes, 1e6 nodes, balanced stencils (FindBalancedSupport reading: "
+                        "per-quadrant quota among the K closest, then the closest of the rest): interior "
+                        "n=25 of K=48, boundary n=30 of K=60; FP32 + refinement weights and 3 operator "
+                        "applications as in the default workload",
+            "K": {"interior": 48, "boundary": 60}}
+
+
+def run_balanced(args, rk):
+    """The default disk step with balanced stencils in place of plain kNN:
+    the selection alone and against plain kNN, the whole step, and sampled
+    rows against the oracle (bit for bit)."""
+    import torch
+    import paper_1912_13282_gb300 as P
+    from oracle import oracle as O
+    device = rk.local
+    stream = torch.cuda.current_stream(device)
+    ctx = P.Context(device, stream)
+    ns, rp = make_disk(rk.rank, args.n_target or DISK["N_target"])
+    pipe = DiskPipeline(P, ctx, ns, rp, device)
+    ni, nb = DISK["interior"]["n"], DISK["boundary"]["n"]
+    Ki, Kb = BALANCED["K"]["interior"], BALANCED["K"]["boundary"]
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=pipe.pts.device)
+
+    def balanced():
+        ctx.balanced_stencils(pipe.pts, [pipe.ranges[0]], Ki, method=P.KNN_GRID)
+        ctx.balanced_stencils(pipe.pts, [pipe.ranges[1]], Kb, method=P.KNN_GRID)
+
+    def timed(fn):
+        flush.add_(1.0)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        z.record(stream)
+        z.synchronize()
+        return a.elapsed_time(z)
+
+    def step():
+        balanced()
+        pipe.weights_interior(P.FP32_IR)
+        pipe.weights_boundary(P.FP32_IR)
+        pipe.apply()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        pipe.knn()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    rk.barrier()
+    sel = [timed(balanced) for _ in range(args.steps)]
+    knn = [timed(pipe.knn) for _ in range(args.steps)]
+    tt = [timed(step) for _ in range(args.steps)]
+    clk = clocks.stop()
+    (ms,) = rk.max([float(np.sum(tt))])
+    (n_all,) = rk.sum([ns.N])
+    # the last step's rows: a sample against the oracle's balanced selection
+    balanced()
+    torch.cuda.synchronize()
+    col = pipe.col.cpu().numpy()
+    rng = np.random.default_rng(3)
+    checked, same = 0, True
+    for (b, e, n, _), K in ((pipe.ranges[0], Ki), (pipe.ranges[1], Kb)):
+        q = np.sort(rng.choice(np.arange(b, e), min(e - b, 400), replace=False))
+        ref, _ = O.balanced(ns.pts, n, K, queries=q, nthreads=O.nthreads_default())
+        got = np.stack([col[rp[i]:rp[i + 1]] for i in q])
+        same &= bool(np.array_equal(got, ref))
+        checked += len(q)
+    st = pipe.status.cpu().numpy()
+    line = {"metric": METRIC + " (balanced stencils)", "value": throughput(n_all, ms, args.steps),
+            "unit": "nodes/s", "n_gpus": rk.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": BALANCED["workload"], "N": ns.N,
+                       "l2": "256 MiB buffer written before every timed launch",
+                       "step": "balanced stencils + weights (2 classes) + 3 operator applications"},
+            "selection_ms": float(np.mean(sel)), "plain_knn_ms": float(np.mean(knn)),
+            "selection_nodes_per_s": ns.N / (float(np.mean(sel)) * 1e-3),
+            "rows_checked_against_oracle": checked, "rows_equal": same,
+            "fallback_fraction": float((st == P.binding.ST_FALLBACK).mean()),
+            "clocks": clk}
+    ctx.close()
+    return line
+
+
+# ----------------------------------------------- 3D convection-diffusion
+CONVDIFF = {"workload": "implicit 3D convection-diffusion (Section 3.3 example), -2 lap u + 8 (2, 1, -1) . "
+                        "grad u = f on the unit ball, Dirichlet sphere, u = sin(pi x) sin(pi y) sin(pi z) "
+                        "manufactured: n=35 r^3 deg 2 stencils, lap/dx/dy/dz weights (FP32 + refinement) "
+                        "combined by eq. gen-op, identity Dirichlet rows, ILU(0) + BiCGSTAB to 1e-10",
+            "N_target": 50_000, "n": 35, "k": 3, "m": 2, "coef": (-2.0, 16.0, 8.0, -8.0), "tol": 1e-10}
+
+
+def run_convdiff(args, rk):
+    import torch
+
+    import nodesets as NS
+    import paper_1912_13282_gb300 as P
+    device = rk.local
+    stream = torch.cuda.current_stream(device)
+    ctx = P.Context(device, stream)
+    ns = NS.ball(args.n_target or CONVDIFF["N_target"], seed=rk.rank)
+    N, n = ns.N, CONVDIFF["n"]
+    nb = ns.classes["boundary"][0]
+    dv = f"cuda:{device}"
+    pts = torch.from_numpy(ns.pts).to(dv)
+    rp = torch.arange(N + 1, dtype=torch.int64, device=dv) * n
+    col = torch.empty(N * n, dtype=torch.int32, device=dv)
+    terms = [torch.zeros(N * n, dtype=torch.float64, device=dv) for _ in range(4)]
+    coefs = [torch.full((N,), c, dtype=torch.float64, device=dv) for c in CONVDIFF["coef"]]
+    L = torch.zeros(N * n, dtype=torch.float64, device=dv)
+    kind = torch.from_numpy(ns.dirichlet.astype(np.uint8)).to(dv)
+    cs, vs = torch.empty_like(col), torch.empty_like(L)
+    fac = torch.empty_like(vs)
+    diag = torch.empty(N, dtype=torch.int64, device=dv)
+    x = torch.zeros(N, dtype=torch.float64, device=dv)
+    u = NS.sin_product(ns.pts)
+    g = NS.sin_product_grad(ns.pts)
+    c0, c1, c2, c3 = CONVDIFF["coef"]
+    f = c0 * NS.sin_product_lap(ns.pts) + c1 * g[:, 0] + c2 * g[:, 1] + c3 * g[:, 2]
+    b = torch.from_numpy(np.where(ns.dirichlet, u, f)).to(dv)
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        ctx.knn_stencils(pts, [(0, N, n, col)], method=P.KNN_GRID)
+        ctx.rbffd_weights(P.LAP | P.DX | P.DY | P.DZ, CONVDIFF["k"], CONVDIFF["m"], pts, rp, col, terms,
+                          row_begin=0, row_end=nb, n_max=n, precision=P.FP32_IR)
+        ctx.combine_operators(rp, col, terms, coefs, L, row_begin=0, row_end=nb)
+        ev[1].record(stream)
+        ctx.implicit_assemble(rp, col, L, kind, cs, vs)
+        ctx.ilu0(rp, cs, vs, fac, diag)
+        ev[2].record(stream)
+        x.zero_()
+        rc, it, res = ctx.bicgstab(rp, cs, vs, b, x, fac, diag, tol=CONVDIFF["tol"], maxit=20000)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        if rc != P.binding.MM_OK:
+            raise RuntimeError(f"BiCGSTAB did not converge: rc={rc} it={it} res={res}")
+        return [ev[0].elapsed_time(ev[3]), ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                ev[2].elapsed_time(ev[3]), it, res]
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    rk.barrier()
+    rows = [step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    R = np.array(rows)
+    (ms,) = rk.max([float(R[:, 0].sum())])
+    (n_all,) = rk.sum([N])
+    iters = int(R[0, 4])
+    line = {"metric": "implicit 3D convection-diffusion unknowns/s (kNN + weights + combination + assembly "
+                      "+ ILU(0) + BiCGSTAB)",
+            "value": throughput(n_all, ms, args.steps), "unit": "unknowns/s", "n_gpus": rk.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": CONVDIFF["workload"], "N": N, "h": ns.h},
+            "breakdown_ms": {"knn_weights_combination": float(R[:, 1].mean()),
+                             "assemble_and_ilu0": float(R[:, 2].mean()), "bicgstab": float(R[:, 3].mean())},
+            "iterations": iters, "relative_residual": float(R[0, 5]),
+            "ms_per_iteration": float(R[:, 3].mean()) / max(iters, 1),
+            "max_error": float(np.abs(x.cpu().numpy() - u).max()), "clocks": clk}
+    ctx.close()
+    return line
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     """The CPU oracle as the reference arm: each step a bounded sample of
@@ -1536,7 +1706,8 @@ def main(argv=None):
         _build.build()
     rk.barrier()
     run = {"disk": run_disk, "ball": run_ball, "batch": run_batch, "surrogate": run_surrogate,
-           "wls": run_wls, "poisson": run_poisson, "square": run_square}[args.workload]
+           "wls": run_wls, "poisson": run_poisson, "square": run_square, "balanced": run_balanced,
+           "convdiff": run_convdiff}[args.workload]
     line = run(args, rk)
     if rk.rank == 0:
         print(json.dumps(line), flush=True)
