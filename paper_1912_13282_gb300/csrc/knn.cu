@@ -22,7 +22,7 @@
 //    and stops once the ring boundary is farther than the n-th best.
 //  * brute: every node is a candidate (for small N).
 // The top n-1 list lives in registers across the warp (two slots per lane,
-// n <= 65) and is kept sorted by warp-wide insertion, or by a bitonic merge
+// up to 64 entries) and is kept sorted by warp-wide insertion, or by a bitonic merge
 // when a batch brings many new entries.
 #include <float.h>
 #include <math.h>

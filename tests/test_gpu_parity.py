@@ -95,7 +95,9 @@ def test_knn_ragged_and_edge_sizes(P, ctx, oracle):
     pts = rng.uniform(size=(1237, 2))
     pts_d = dev(pts)
     for method in (P.KNN_GRID, P.KNN_BRUTE):
-        ranges = [(7, 1000, 1), (1000, 1237, 64), (3, 5, 33)]
+        # the top list holds n - 1 entries: n = 33 is the largest one-slot
+        # list, n = 34 the smallest two-slot one, n = 64 the largest allowed
+        ranges = [(7, 1000, 1), (1000, 1237, 64), (3, 5, 33), (20, 400, 34), (400, 900, 64), (900, 1100, 33)]
         got, _ = gpu_knn(ctx, P, pts_d, ranges, method)
         for (b, e, n), g in zip(ranges, got):
             ref, _ = oracle.knn(pts, n, queries=np.arange(b, e))
