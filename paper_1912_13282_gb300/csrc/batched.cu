@@ -54,24 +54,34 @@ struct BatchParams {
 
 static_assert(sizeof(BatchParams) <= 32000, "batched kernel parameters exceed the 32 KB limit");
 
-// Variant of a class for the mixed kernel: (dim, rows per lane, column count).
-// Classes with 2..4 operators run on the 4-column solver (the unused columns
-// carry a zero right-hand side and are not stored).
+// Variant of a class for the mixed kernel: (dim, rows per lane, column count)
+// with the shared-memory inverse (0..11), or (dim, register width, column
+// count) with the register-resident inverse (12..19), which the per-class
+// launch also takes for systems of 33..48 unknowns padded to 40 or 48
+// columns.  Both inverses give the same bits.  Classes with 2..4 operators
+// run on the 4-column solver (the unused columns carry a zero right-hand
+// side and are not stored).
 __host__ __device__ inline int mixed_cols(int R) { return R == 1 ? 1 : 4; }
-__host__ __device__ inline int mixed_variant(int dim, int rpl, int R) {
+__host__ __device__ inline int mixed_variant(int dim, int rpl, int R, int wreg) {
     const int rsel = R == 1 ? 0 : 1;
+    if (wreg) return 12 + ((dim - 2) * 2 + (wreg == 48 ? 1 : 0)) * 2 + rsel;
     return ((dim - 2) * 3 + (rpl - 1)) * 2 + rsel;
 }
 
-template <int DIM, int RPL>
+template <int DIM, int RPL, int W = 0>
 __device__ bool mixed_dispatch_r(int rsel, const WParams &P, int64_t row, char *base) {
-    if (rsel == 0) return mixed_row<DIM, RPL, 1>(P, row, base);
-    return mixed_row<DIM, RPL, 4>(P, row, base);
+    if (rsel == 0) return mixed_row<DIM, RPL, 1, W>(P, row, base);
+    return mixed_row<DIM, RPL, 4, W>(P, row, base);
 }
 
 template <int DIM>
 __device__ bool mixed_dispatch_d(int v, const WParams &P, int64_t row, char *base) {
-    const int rsel = v % 2, rpl = (v / 2) % 3 + 1;
+    const int rsel = v % 2;
+    if (v >= 12) {
+        if (((v - 12) >> 1) & 1) return mixed_dispatch_r<DIM, 2, 48>(rsel, P, row, base);
+        return mixed_dispatch_r<DIM, 2, 40>(rsel, P, row, base);
+    }
+    const int rpl = (v / 2) % 3 + 1;
     if (rpl == 1) return mixed_dispatch_r<DIM, 1>(rsel, P, row, base);
     if (rpl == 2) return mixed_dispatch_r<DIM, 2>(rsel, P, row, base);
     return mixed_dispatch_r<DIM, 3>(rsel, P, row, base);
@@ -88,7 +98,7 @@ __device__ int class_of(const BatchParams &B, int64_t item, int cb, int ce) {
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_weights_batched(const __grid_constant__ BatchParams B) {
+__device__ __forceinline__ void batched_body(const BatchParams &B) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int cb = 0;
@@ -126,6 +136,17 @@ __global__ void __launch_bounds__(256) k_weights_batched(const __grid_constant__
         __syncthreads();
         cb = ce;
     }
+}
+
+// The FP32 + refinement kernel is held to 168 registers (the register-resident
+// inverse's budget in the per-class launch: 12 warps per SM); 8-warp CTAs
+// still fit (168 x 256 registers).
+__global__ void __maxnreg__(168) k_weights_batched_mixed(const __grid_constant__ BatchParams B) {
+    batched_body<true>(B);
+}
+
+__global__ void __launch_bounds__(256) k_weights_batched_fp64(const __grid_constant__ BatchParams B) {
+    batched_body<false>(B);
 }
 
 __global__ void __launch_bounds__(256) k_weights_batched_fallback(const __grid_constant__ BatchParams B) {
@@ -211,8 +232,11 @@ int prepare(mm_ctx *ctx, int nclasses, const mm_weights_class *classes, int prec
 }
 
 // Phase plan for W warps per CTA: shared memory S = max(W * smallest
-// footprint, largest footprint) (capped by the device), classes ordered by the
-// number of stencils that fit in S at once, descending.
+// footprint, largest footprint) (capped by the device), grown to the most
+// that keeps as many CTAs resident per SM (whole KB), so a class of larger
+// stencils runs as many of them per CTA as that room allows (3 of the 3D
+// refined class in one 8-warp CTA per SM instead of 2); classes ordered by
+// the number of stencils that fit in S at once, descending.
 int build_params(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg, BatchParams &B,
                  size_t &smem) {
     const int W = cfg.warps_per_block;
@@ -221,6 +245,11 @@ int build_params(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg, B
     for (size_t f : pr.foot) { fmin = std::min(fmin, f); fmax = std::max(fmax, f); }
     if (fmax > ctx->smem_optin) return mm_fail(ctx, MM_EUNSUPPORTED, "batched: %zu bytes of shared memory per stencil", fmax);
     smem = std::min(std::max((size_t)W * fmin, fmax), (size_t)ctx->smem_optin);
+    if (ctx->smem_per_sm > smem + ctx->smem_reserved) {
+        const size_t ncta = ctx->smem_per_sm / (smem + ctx->smem_reserved);
+        const size_t room = (ctx->smem_per_sm / ncta - ctx->smem_reserved) & ~size_t(1023);
+        smem = std::max(smem, std::min(room, (size_t)ctx->smem_optin));
+    }
     std::vector<int> order(nc), fit(nc);
     for (int i = 0; i < nc; ++i) {
         order[i] = i;
@@ -236,7 +265,11 @@ int build_params(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg, B
         const int i = order[j];
         const WParams &P = pr.cls[i];
         B.cls[j] = P;
-        if (pr.mixed) B.variant[j] = (signed char)mixed_variant(P.dim, (P.M_max + 31) / 32, P.R);
+        if (pr.mixed) {
+            const int rpl = (P.M_max + 31) / 32, w4 = 4 * ((P.M_max + 3) / 4);
+            const int wreg = rpl == 2 && !ctx->gj_shared && (w4 == 40 || w4 == 48) ? w4 : 0;
+            B.variant[j] = (signed char)mixed_variant(P.dim, rpl, P.R, wreg);
+        }
         B.prefix[j] = items;
         items += (P.row_end - P.row_begin + cfg.chunk_rows - 1) / cfg.chunk_rows;
         const bool new_phase = B.nphases == 0 || B.phase_warps[B.nphases - 1] != fit[i];
@@ -286,7 +319,7 @@ int launch_prepared(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg
     B.fb_count = B.queue + B.nphases;
     B.fb_list = pr.mixed ? (u64 *)(ws + o_fb) : nullptr;
     cudaStream_t st = ctx->stream;
-    const void *kern = pr.mixed ? (const void *)k_weights_batched<true> : (const void *)k_weights_batched<false>;
+    const void *kern = pr.mixed ? (const void *)k_weights_batched_mixed : (const void *)k_weights_batched_fp64;
     cudaError_t e = cudaMemsetAsync(B.queue, 0, sizeof(int) * (B.nphases + 1), st);
     if (e == cudaSuccess) e = mm_set_smem(ctx, kern, sm);
     int per_sm = cfg.blocks_per_sm;
@@ -297,8 +330,8 @@ int launch_prepared(mm_ctx *ctx, const Prepared &pr, const mm_launch_config &cfg
     }
     if (e != cudaSuccess) { delete Bp; return mm_fail(ctx, MM_ECUDA, "batched launch setup: %s", cudaGetErrorString(e)); }
     const int blocks = per_sm * ctx->num_sms;
-    if (pr.mixed) k_weights_batched<true><<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
-    else k_weights_batched<false><<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
+    if (pr.mixed) k_weights_batched_mixed<<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
+    else k_weights_batched_fp64<<<blocks, cfg.warps_per_block * 32, sm, st>>>(B);
     e = cudaGetLastError();
     if (e == cudaSuccess && pr.mixed) {
         const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / pr.fb_slot));
@@ -389,7 +422,7 @@ int mm_autotune_batched(mm_ctx *ctx, int nclasses, const mm_weights_class *class
         delete Bp;
         ctx->err.clear();
         if (!fits || sm > ctx->smem_optin) continue;
-        const void *kern = pr.mixed ? (const void *)k_weights_batched<true> : (const void *)k_weights_batched<false>;
+        const void *kern = pr.mixed ? (const void *)k_weights_batched_mixed : (const void *)k_weights_batched_fp64;
         if (mm_set_smem(ctx, kern, sm) != cudaSuccess) { cudaGetLastError(); continue; }
         int occ = 0;
         if (occupancy(ctx, kern, wpb * 32, sm, &occ) != cudaSuccess || occ < 1) {
