@@ -76,6 +76,9 @@ def parse(argv=None):
                                                           "square", "balanced", "convdiff"])
     ap.add_argument("--n-target", type=int, default=None, help="override the node count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-config", default=None,
+                    help="ball: fixed launch shape 'warps_per_block,blocks_per_sm,chunk_rows' for both "
+                         "precisions instead of the autotuner's")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--no-poisson", action="store_true")
@@ -808,15 +811,24 @@ def run_ball(args, rk):
     y = torch.empty_like(u)
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dv)
 
+    fixed = tuple(int(v) for v in args.batched_config.split(",")) if args.batched_config else None
+
+    def weights(prec):
+        ctx.rbffd_weights_batched(classes, precision=prec, config=fixed)
+
     def step(prec):
         ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
-        ctx.rbffd_weights_batched(classes, precision=prec)
+        weights(prec)
         for v in vals:
             ctx.apply_operator(rp_d, col, v, u, y)
 
     ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
     tuned = {}
     for name, prec in (("fp64", P.FP64), ("fp32_ir", P.FP32_IR)):
+        if fixed:
+            tuned[name] = {"warps_per_block": fixed[0], "blocks_per_sm": fixed[1], "chunk_rows": fixed[2],
+                           "fixed": True}
+            continue
         cfg, t = ctx.autotune_batched(classes, precision=prec, sample_rows=32768)
         tuned[name] = {"warps_per_block": cfg[0], "blocks_per_sm": cfg[1], "chunk_rows": cfg[2],
                        "sample_ms": t}
@@ -836,7 +848,7 @@ def run_ball(args, rk):
             ev[0].record(stream)
             ctx.knn_stencils(pts, ranges, method=P.KNN_GRID)
             ev[1].record(stream)
-            ctx.rbffd_weights_batched(classes, precision=prec)
+            weights(prec)
             ev[2].record(stream)
             for v in vals:
                 ctx.apply_operator(rp_d, col, v, u, y)
