@@ -94,7 +94,8 @@ def test_batched_equals_per_class(P, precision):
         g.per_class(P, ctx, v, prec)
         torch.cuda.synchronize()
         ref.append(({b: t.cpu().numpy() for b, t in v.items()}, g.status.cpu().numpy().copy()))
-    for cfg in (None, (1, 1, 4), (2, 0, 64)):
+    # (8, 1, 4): one 8-warp CTA per SM, shared memory grown to the whole SM
+    for cfg in (None, (1, 1, 4), (2, 0, 64), (8, 1, 4)):
         outs, classes = [], []
         for g in geoms:
             v = g.new_vals()
